@@ -1,0 +1,318 @@
+"""Benchmark: CTF-MNMF-ISS iterations/s on one GB300 (and N independent replicas).
+
+A step is one full solve of the plain single-mixture workload through the C ABI:
+load the STFT, set the NMF init, run 100 iterations (ISS sweep + basis MU per bin,
+activation MU + normalisation across bins). Workload: N=2 sources, M=3 microphones,
+taps (2,1), F=513 bins, J=1000 frames, B=10 bases, seeded synthetic CTF mixture
+(16 kHz speech-like shape, STFT 1024 / hop 256, -30 dB noise).
+
+  value  : iterations/s of the whole job (all ranks), CUDA events on the solver's stream,
+           inputs resident in HBM, L2 flushed (256 MiB write) between steps
+  e2e    : the same through host buffers (pinned X, T0, V0 in; separated images out)
+  roofline: the dominant kernel's algorithmic bytes per launch / its event-timed duration
+
+--impl reference times the FP64 CPU oracle (one iteration of the same workload per step).
+Under torchrun each rank solves its own mixture (seed = rank): weak scaling, no collective
+on the data path; only the timing uses a barrier and a max-reduce.
+"""
+import os
+import sys
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CTF-MNMF-ISS iterations/s at 1 GB300 (plain vs batched vs fwd+bwd), % HBM roof"
+UNIT = "iterations/s"
+WORKLOAD = "C2"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--iters", type=int, default=None, help="iterations per step (default: workload's)")
+    return p.parse_args()
+
+
+def spec_for(rank):
+    from paper_2510_02382_gb300 import synth
+    return synth.scaled(synth.CONFIGS[WORKLOAD], seed=rank)
+
+
+def workload_config(spec, l2_note):
+    return {"workload": f"{WORKLOAD}: plain CTF-MNMF-ISS, N={spec.N} M={spec.M} taps={tuple(spec.taps())} "
+                        f"F={spec.F} J={spec.J} B={spec.B}, {spec.iters} iterations per solve",
+            "N": spec.N, "M": spec.M, "F": spec.F, "J": spec.J, "B": spec.B,
+            "iterations_per_step": spec.iters, "l2": l2_note, "replicas": "one mixture per rank (seed = rank)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_sample(seconds=12.0):
+    """The FP64 oracle, as it stands, on one host core: iterations of the full workload
+    until `seconds` have passed (at least 2). Runs in a fresh interpreter."""
+    code = f"""
+import os, time, json, sys
+sys.path.insert(0, {ROOT!r})
+from paper_2510_02382_gb300 import synth
+from oracle import ctfmnmf_oracle as O
+spec = synth.CONFIGS[{WORKLOAD!r}]
+mix = synth.make_mixture(spec)
+x, W, b, v = O.init_state(mix.X, mix.T0, mix.V0)
+n, t0 = 0, time.perf_counter()
+while n < 2 or time.perf_counter() - t0 < {seconds}:
+    W, b, v, y = O.iterate(x, W, b, v, mix.Ln)
+    n += 1
+dt = time.perf_counter() - t0
+print(json.dumps({{"iters": n, "seconds": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if res.returncode != 0:
+        return None
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['iters']} FP64 oracle iterations of the full {WORKLOAD} mixture in {d['seconds']:.1f} s "
+                      f"(single thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import ctfmnmf_oracle as O
+    from paper_2510_02382_gb300 import synth
+    spec = spec_for(0)
+    mix = synth.make_mixture(spec)
+    x, W, b, v = O.init_state(mix.X, mix.T0, mix.V0)
+    for _ in range(args.warmup):
+        W, b, v, y = O.iterate(x, W, b, v, mix.Ln)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, b, v, y = O.iterate(x, W, b, v, mix.Ln)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = f"one FP64 oracle iteration of the full {WORKLOAD} mixture per step (single thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(spec, "host CPU run"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    from paper_2510_02382_gb300 import synth
+    from paper_2510_02382_gb300.api import CTFMNMF
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    spec = spec_for(rank)
+    iters = args.iters or spec.iters
+    mix = synth.make_mixture(spec)
+    N, M, F, J, B = spec.N, spec.M, spec.F, spec.J, spec.B
+    stream = torch.cuda.current_stream()
+    solver = CTFMNMF(M, N, spec.L, B, F, J, Ln=mix.Ln, stream=stream)
+    X_h = torch.from_numpy(mix.X).pin_memory()
+    T0_h = torch.from_numpy(mix.T0).pin_memory()
+    V0_h = torch.from_numpy(mix.V0).pin_memory()
+    X_d, T0_d, V0_d = X_h.cuda(), T0_h.cuda(), V0_h.cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    def step():
+        solver.load_stft(X_d)
+        solver.set_init(T0_d, V0_d)
+        solver.iterate(iters)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = solver.launch_count()
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    barrier()
+    launches = solver.launch_count() - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    clocks = sampler.stop() if sampler else None
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * iters * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through host buffers
+    out_h = torch.empty((N, M, F, J), dtype=torch.complex64).pin_memory()
+    T0_e = torch.empty_like(T0_d)
+    V0_e = torch.empty_like(V0_d)
+
+    def step_e2e():
+        solver.load_stft(X_h)
+        T0_e.copy_(T0_h, non_blocking=True)
+        V0_e.copy_(V0_h, non_blocking=True)
+        solver.set_init(T0_e, V0_e)
+        solver.iterate(iters)
+        solver.get_separated(out_h)
+
+    step_e2e()
+    e2e_steps = max(1, min(args.steps, 50))
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    barrier()
+    for k in range(e2e_steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        step_e2e()
+        ev2[k][1].record(stream)
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * iters * e2e_steps / (float(t.item()) / 1000.0)
+    h2d = X_h.numel() * 8 + T0_h.numel() * 4 + V0_h.numel() * 4
+    d2h = out_h.numel() * 8
+
+    # ---- per-kernel durations (event pairs around each launch, same stream) for the roofline
+    solver.load_stft(X_d)
+    solver.set_init(T0_d, V0_d)
+    solver.time_phases(5)
+    ms_bin, ms_frame = solver.time_phases(50)
+    bytes_bin = 16 * M * F * J + 8 * N * B * F + 4 * N * B * J
+    bytes_frame = 8 * N * F * J + 4 * N * F * B + 8 * N * B * J
+    if ms_bin >= ms_frame:
+        kname, kms, kbytes = "bin_phase_kernel", ms_bin, bytes_bin
+    else:
+        kname, kms, kbytes = "frame_phase_kernel", ms_frame, bytes_frame
+    peak, peak_src = peaks()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    solver.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline_sample() if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(spec, "flushed between steps (256 MiB write outside the timed events)"),
+        "bin_frames_per_s": value * F * J,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms},
+        "phase_ms": {"bin_phase": ms_bin, "frame_phase": ms_frame},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * ctfmnmf.h -- C ABI of libctfmnmf: CTF-MNMF with iterative source steering (ISS)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Xie, Wang, Zhang, Yang, Makino, "Accelerated Convolutive Transfer
+ * Function-Based Multichannel NMF Using Iterative Source Steering" (APSIPA ASC 2025).
+ *   - extended instantaneous model, rows r <-> (source n, tap l), sum_n L_n = M   (Sec. II, Eq. 3)
+ *   - demixing y_{r,i,j} = w_r^H x_{i,j}                                          (Eq. 4)
+ *   - NMF source model lambda_{n,i,j} = sum_k T[n,i,k] V[n,k,j]                    (Sec. II)
+ *   - negative log-likelihood                                                     (Eq. 5)
+ *   - ISS rank-1 updates W_i <- W_i - z_r w_r^H with the closed form of Eq. 16    (Sec. III-A)
+ *   - multiplicative updates of T (Eq. 17) and V (Eq. 18), scale normalisation    (Sec. III-B)
+ *   - source images by the multichannel Wiener filter                            (Eqs. 23-24)
+ *
+ * Conventions for every entry point:
+ *   - The return value is a ctfmnmf_status: 0 on success, a negative code on failure.
+ *     No call aborts, traps or exits the process. After a failure,
+ *     ctfmnmf_last_error(h) returns a short static description.
+ *   - "device pointer" means memory of the GPU current when the handle was created
+ *     (cudaMalloc or a torch CUDA tensor). The caller owns every pointer it passes;
+ *     the library never frees or retains caller memory after the call returns.
+ *   - "host pointer" means ordinary or pinned CPU memory.
+ *   - complex64 = two float32 (re, im), interleaved, as cuFloatComplex / torch.complex64.
+ *   - Arrays are dense, C order, with the stated shapes and no padding.
+ *   - Dimensions: M microphones, N sources, B NMF bases per source (the paper's K_n),
+ *     F frequency bins (the paper's I), J frames, L_n taps of source n with sum L_n = M.
+ *   - Work is enqueued on the handle's stream (ctfmnmf_set_stream; default: the legacy
+ *     default stream) and is asynchronous unless the entry point says it synchronises.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by the caller.
+ */
+#ifndef CTFMNMF_H
+#define CTFMNMF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CTFMNMF_MAX_M 8   /* most microphones (= extended rows) per mixture          */
+#define CTFMNMF_MAX_B 32  /* most NMF bases per source                                */
+
+typedef enum ctfmnmf_status {
+    CTFMNMF_OK = 0,
+    CTFMNMF_EINVAL = -1,       /* bad argument: shape, null pointer, option value          */
+    CTFMNMF_ESTATE = -2,       /* call out of order, e.g. iterate before load_stft         */
+    CTFMNMF_ECUDA = -3,        /* a CUDA runtime call failed                              */
+    CTFMNMF_ENONFINITE = -4,   /* the input STFT or NMF factors hold NaN or Inf          */
+    CTFMNMF_ETIMEOUT = -5,     /* a bounded device-side wait gave up                     */
+    CTFMNMF_ENOMEM = -6,       /* device allocation failed                                */
+    CTFMNMF_EUNSUPPORTED = -7  /* valid shape that these kernels do not handle (see create) */
+} ctfmnmf_status;
+
+/* Activation update variants (Eq. 18). */
+enum {
+    CTFMNMF_V_ALL_TAPS = 0,    /* default: sum over all taps of the source, the
+                                  majorisation-minimisation form of Eq. 18            */
+    CTFMNMF_V_TAP0 = 1         /* Eq. 18 as printed: tap l = 0 only                    */
+};
+
+typedef struct ctfmnmf_dims {
+    int M, N, L, B, F, J;      /* L: cap on taps per source (and the length of the
+                                  mixing CTF the data was made with)                   */
+} ctfmnmf_dims;
+
+typedef struct ctfmnmf_options {
+    int v_update;              /* CTFMNMF_V_ALL_TAPS (default) or CTFMNMF_V_TAP0        */
+    int normalize;             /* 1 (default): scale normalisation of Eqs. 19-21 after
+                                  every iteration; 0: none                              */
+    int use_graph;             /* 1 (default): ctfmnmf_iterate replays a CUDA graph of
+                                  its launches; 0: plain stream launches                */
+    int reserved[5];           /* must be zero                                          */
+} ctfmnmf_options;
+
+typedef struct ctfmnmf* ctfmnmf_t;
+
+/* Fill *opt with the defaults listed above. */
+void ctfmnmf_default_options(ctfmnmf_options* opt);
+
+/*
+ * Create a solver for one mixture on the current CUDA device and allocate its
+ * device state (about 8*M*F*J + 12*N*F*J + 4*N*B*J + 8*M*M*F bytes).
+ * Taps: L_n = floor(M/N) + (n < M mod N), each at most L, so that sum L_n = M
+ * (the square model of Sec. II; M=4,6,8 with N=2 gives the paper's Table I).
+ * EINVAL if a dimension is <= 0, N > M, M > CTFMNMF_MAX_M, B > CTFMNMF_MAX_B,
+ * a derived L_n exceeds L, J <= max L_n, or out is NULL.
+ * EUNSUPPORTED if J exceeds 4096 (M <= 4) or 2048 (M = 5..8).
+ * On success *out receives the handle; on failure *out is set to NULL.
+ */
+int ctfmnmf_create(int M, int N, int L, int B, int F, int J, ctfmnmf_t* out);
+
+/* As ctfmnmf_create, with explicit taps Ln[N] (NULL: derived as above; sum must be M)
+ * and options (NULL: defaults). dims->L only bounds the taps. */
+int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_options* opt,
+                      ctfmnmf_t* out);
+
+/* Release every device buffer of h. h may be NULL. Synchronises h's stream first. */
+int ctfmnmf_destroy(ctfmnmf_t h);
+
+/* Short static description of the last failure on h (h NULL: last failed create on this
+ * thread). Never NULL; "" if nothing failed. Valid until the next call on h. */
+const char* ctfmnmf_last_error(ctfmnmf_t h);
+
+/* Use stream (a cudaStream_t, NULL = legacy default stream) for all later work on h. */
+int ctfmnmf_set_stream(ctfmnmf_t h, void* stream);
+
+/* Write the taps L_n of h into Ln[N] (host). */
+int ctfmnmf_get_taps(ctfmnmf_t h, int* Ln);
+
+/*
+ * Load the observed STFT X (device pointer, complex64 [M][F][J], read only during the
+ * call's stream work) and reset the demixing state: W_i = I, y = x, log|det W_i| = 0
+ * (initialisation of Sec. IV-A). T and V are not changed: they keep the default init of
+ * ctfmnmf_create, the values of ctfmnmf_set_init or the result of earlier iterations.
+ * Synchronises the stream to check X:
+ * ENONFINITE if X holds NaN or Inf (the state is then unusable until a good load).
+ */
+int ctfmnmf_load_stft(ctfmnmf_t h, const void* X);
+
+/* As ctfmnmf_load_stft with X a host pointer (complex64 [M][F][J]); the copy to the
+ * device is part of the call. Pinned memory gives the fastest copy. */
+int ctfmnmf_load_stft_host(ctfmnmf_t h, const void* X);
+
+/*
+ * Set the NMF factors (device pointers, float32): T0 [N][F][B] (bases b_{n,i,k}) and
+ * V0 [N][B][J] (activations v_{n,k,j}); values are floored at 1e-12. Either may be
+ * NULL to keep the current value. Without this call, T and V start from the default
+ * init: element e (flat C-order index) of T0 is 0.1 + 0.9*u(2e), of V0 0.1 + 0.9*u(2e+1),
+ * u(c) = top 24 bits of splitmix64(seed * 2^32 + c) / 2^24, seed 0.
+ * Synchronises the stream to check the values: ENONFINITE if any is NaN or Inf.
+ */
+int ctfmnmf_set_init(ctfmnmf_t h, const float* T0, const float* V0);
+
+/*
+ * Run n_iter >= 0 iterations (Sec. III): for each frequency bin the ISS sweep over the
+ * M extended rows (Eqs. 11-16), the basis MU (Eq. 17), then the activation MU over all
+ * bins (Eq. 18), then the scale normalisation (Eqs. 19-21). Asynchronous.
+ * ESTATE if no STFT has been loaded.
+ */
+int ctfmnmf_iterate(ctfmnmf_t h, int n_iter);
+
+/*
+ * Negative log-likelihood of Eq. 5 without its constant, at the current state:
+ * sum over bins, rows r=(n,l) and frames j >= l of log lambda_{n,i,j-l} +
+ * |y_{r,i,j}|^2 / lambda_{n,i,j-l}, minus 2 J sum_i log|det W_i|.
+ * Writes one double to *out (host). Synchronises the stream.
+ */
+int ctfmnmf_cost(ctfmnmf_t h, double* out);
+
+/*
+ * Source images by the multichannel Wiener filter of Eqs. 23-24; under the square model
+ * it reduces to c_n = sum_l [W_i^{-1}]_{:,(n,l)} y_{(n,l),i,j}. Out: device pointer,
+ * complex64 [N][M][F][J]. Asynchronous.
+ */
+int ctfmnmf_get_separated(ctfmnmf_t h, void* C);
+
+/* As ctfmnmf_get_separated into a host buffer; synchronises the stream. */
+int ctfmnmf_get_separated_host(ctfmnmf_t h, void* C);
+
+/* Demixed extended rows y_{r,i,j} (Eq. 4): device pointer, complex64 [M][F][J]. */
+int ctfmnmf_get_demixed(ctfmnmf_t h, void* Y);
+
+/* Demixing matrices: device pointer, complex64 [F][M][M]; element [i][r][m] is the
+ * coefficient of x_m in y_r, i.e. row r of W_i is w_r^H. */
+int ctfmnmf_get_demix_matrix(ctfmnmf_t h, void* W);
+
+/* log|det W_i| per bin, tracked through the determinant lemma: device pointer,
+ * float64 [F]. */
+int ctfmnmf_get_logdet(ctfmnmf_t h, double* logdet);
+
+/* NMF factors: device pointers, float32 T [N][F][B] and V [N][B][J]; either may be NULL. */
+int ctfmnmf_get_nmf(ctfmnmf_t h, float* T, float* V);
+
+/* ---- diagnostics (not part of the method) ---- */
+
+/*
+ * Run n_iter >= 1 iterations exactly like ctfmnmf_iterate but as plain stream launches
+ * with a CUDA event pair around every launch, synchronise, and write to ms[2] (host) the
+ * average device time in milliseconds of one launch of the bin-phase kernel (ISS sweep and
+ * basis update, ms[0]) and of the frame-phase kernel (activation update and normalisation,
+ * ms[1]). The state advances by n_iter iterations.
+ */
+int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms);
+
+/* Number of kernels this handle has enqueued since it was created (host counter; a graph
+ * replay counts every kernel node in it). Writes one int64 to *count (host). */
+int ctfmnmf_get_launch_count(ctfmnmf_t h, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTFMNMF_H */

@@ -66,13 +66,13 @@ def delayed_weights(lam, Ln):
 
 
 def weighted_covariances(x, phi):
-    """Q_{r,i} = (1/J) sum_j x_{i,j} x_{i,j}^H / lambda_{n,i,j-l}  (Eq. 7), [M][I][M][M]."""
+    """Q_{r,i} = (1/J) sum_j x_{i,j} x_{i,j}^H / lambda_{n,i,j-l}  (Eq. 8), [M][I][M][M]."""
     J = x.shape[2]
     return np.einsum("rij,imj,ikj->rimk", phi, x, x.conj()) / J
 
 
 def aux_value(W, Q):
-    """Auxiliary function of Eq. 6 per bin: -2 log|det W_i| + sum_r w_r^H Q_{r,i} w_r."""
+    """Auxiliary function of Eq. 7 per bin: -2 log|det W_i| + sum_r w_r^H Q_{r,i} w_r."""
     M = W.shape[1]
     val = -2.0 * np.log(np.abs(np.linalg.det(W)))
     for r in range(M):
@@ -82,7 +82,7 @@ def aux_value(W, Q):
 
 
 def iss_sweep(W, Q):
-    """One ISS sweep (Eqs. 10-13): for r = 0..M-1 in order, W_i <- W_i - z_r w_r^H.
+    """One ISS sweep (Eqs. 11-16): for r = 0..M-1 in order, W_i <- W_i - z_r w_r^H.
 
     z_p = (w_p^H Q_p w_r) / (w_r^H Q_p w_r) for p != r and z_r = 1 - (w_r^H Q_r w_r)^{-1/2},
     evaluated with the current W (the rows change after every step). Returns the new
@@ -110,7 +110,7 @@ def iss_sweep(W, Q):
 
 
 def ip_sweep(W, Q):
-    """One IP sweep (Eqs. 8-9): w_r <- (W Q_r)^{-1} e_r, w_r <- w_r (w_r^H Q_r w_r)^{-1/2}."""
+    """One IP sweep (Eqs. 9-10): w_r <- (W Q_r)^{-1} e_r, w_r <- w_r (w_r^H Q_r w_r)^{-1/2}."""
     W = W.copy()
     I, M, _ = W.shape
     for r in range(M):
@@ -138,7 +138,7 @@ def _delayed_power(y, Ln, n, J):
 
 
 def update_basis(b, v, y, Ln):
-    """Basis MU of Eq. 14 with l over the taps of source n and masked j-l < 0.
+    """Basis MU of Eq. 17 with l over the taps of source n and masked j-l < 0.
 
     b_{n,i,k} <- b sqrt( sum_{j,l} |y_{n,i,j,l}|^2 v_{n,k,j-l} lam_{n,i,j-l}^{-2}
                        / sum_{j,l} v_{n,k,j-l} lam_{n,i,j-l}^{-1} )
@@ -158,7 +158,7 @@ def update_basis(b, v, y, Ln):
 
 
 def update_activation(b, v, y, Ln, mode="all_taps"):
-    """Activation MU of Eq. 15.
+    """Activation MU of Eq. 18.
 
     "tap0" (as printed): v_{n,k,j} <- v sqrt( sum_i |y_{n,i,j,0}|^2 b lam^{-2} / sum_i b lam^{-1} ).
     "all_taps" (default): the same with |y_{n,i,j,0}|^2 replaced by the delayed power of all
@@ -183,7 +183,7 @@ def update_activation(b, v, y, Ln, mode="all_taps"):
 
 
 def normalise(y, W, b, Ln):
-    """Scale normalisation (Eqs. 16-18): mu_{n,l} = sqrt(mean_{i,j} |y|^2),
+    """Scale normalisation (Eqs. 19-21): mu_{n,l} = sqrt(mean_{i,j} |y|^2),
     y_{n,l} /= mu_{n,l}, the matching row of W /= mu_{n,l}, b_n *= mu_{n,0}^{-2}."""
     rows = row_map(Ln)
     mu = np.sqrt(np.mean(np.abs(y) ** 2, axis=(1, 2)))     # [M]
@@ -213,7 +213,7 @@ def nll(y, lam, W, Ln):
 
 
 def source_images(W, y, Ln):
-    """MWF source images (Eq. 20) under the square model reduce to
+    """MWF source images (Eqs. 23-24) under the square model reduce to
     c_n = sum_l [W_i^{-1}]_{:, (n,l)} y_{(n,l)}; returns [N][M][I][J]."""
     H = np.linalg.inv(W)                                    # [I][M][M]
     rows = row_map(Ln)
@@ -226,7 +226,7 @@ def source_images(W, y, Ln):
 
 
 def mwf_images(W, lam, x, Ln):
-    """Literal multichannel Wiener filter of Eq. 20, c_n = H_n Lam_n H_n^H (H Lam H^H)^{-1} x,
+    """Literal multichannel Wiener filter of Eqs. 23-24, c_n = H_n Lam_n H_n^H (H Lam H^H)^{-1} x,
     with H_i = W_i^{-1} and Lam the diagonal of delayed PSDs lam_{n,i,j-l} (frames j >= max l)."""
     H = np.linalg.inv(W)
     rows = row_map(Ln)

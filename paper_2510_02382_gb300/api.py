@@ -1,0 +1,224 @@
+"""Python binding of libctfmnmf (ctypes): the C ABI of include/ctfmnmf.h, same names.
+
+Argument marshalling only: every step of the method runs in the CUDA library. Device
+memory comes from torch tensors (their data pointers); work runs on the stream given
+to the handle, by default torch's current stream at construction. If the library
+has not been built, loading it raises; there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from .build import lib_path
+
+c_int, c_void_p, c_double, c_char_p = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_char_p
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ESTATE", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
+          -6: "ENOMEM", -7: "EUNSUPPORTED"}
+V_ALL_TAPS, V_TAP0 = 0, 1
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("M", c_int), ("N", c_int), ("L", c_int), ("B", c_int), ("F", c_int), ("J", c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("v_update", c_int), ("normalize", c_int), ("use_graph", c_int),
+                ("reserved", c_int * 5)]
+
+
+class CtfMnmfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+_LIB = None
+
+_SIGS = {
+    "ctfmnmf_default_options": (None, [c_void_p]),
+    "ctfmnmf_create": (c_int, [c_int] * 6 + [c_void_p]),
+    "ctfmnmf_create_ex": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_destroy": (c_int, [c_void_p]),
+    "ctfmnmf_last_error": (c_char_p, [c_void_p]),
+    "ctfmnmf_set_stream": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_taps": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_load_stft": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_load_stft_host": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_set_init": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_iterate": (c_int, [c_void_p, c_int]),
+    "ctfmnmf_cost": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_separated": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_separated_host": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_demixed": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_demix_matrix": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_logdet": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_nmf": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_time_phases": (c_int, [c_void_p, c_int, c_void_p]),
+    "ctfmnmf_get_launch_count": (c_int, [c_void_p, c_void_p]),
+}
+
+
+def lib():
+    """Load libctfmnmf.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        p = lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -m paper_2510_02382_gb300.build`")
+        L = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, h=None):
+    if rc != 0:
+        msg = lib().ctfmnmf_last_error(h)
+        raise CtfMnmfError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+class CTFMNMF:
+    """One mixture's solver on the current CUDA device (a handle of the C ABI).
+
+    Shapes follow the C ABI: X [M][F][J] complex64, T [N][F][B], V [N][B][J] float32,
+    images [N][M][F][J] complex64, W [F][M][M] complex64, logdet [F] float64.
+    """
+
+    def __init__(self, M: int, N: int, L: int, B: int, F: int, J: int,
+                 Ln: Optional[Sequence[int]] = None, v_update: str = "all_taps",
+                 normalize: bool = True, use_graph: bool = True, stream=None):
+        import torch
+        self.M, self.N, self.L, self.B, self.F, self.J = M, N, L, B, F, J
+        d = Dims(M, N, L, B, F, J)
+        o = Options()
+        lib().ctfmnmf_default_options(ctypes.byref(o))
+        o.v_update = {"all_taps": V_ALL_TAPS, "tap0": V_TAP0}[v_update]
+        o.normalize = int(bool(normalize))
+        o.use_graph = int(bool(use_graph))
+        ln_arr = (c_int * N)(*Ln) if Ln is not None else None
+        h = c_void_p()
+        rc = lib().ctfmnmf_create_ex(ctypes.byref(d), ln_arr, ctypes.byref(o), ctypes.byref(h))
+        _check(rc, None)
+        self._h = h
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().ctfmnmf_set_stream(self._h, c_void_p(self.stream.cuda_stream)), self._h)
+        taps = (c_int * N)()
+        _check(lib().ctfmnmf_get_taps(self._h, taps), self._h)
+        self.Ln = list(taps)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ctfmnmf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- inputs
+    def load_stft(self, X):
+        import torch
+        self._expect(X, (self.M, self.F, self.J), torch.complex64)
+        if X.is_cuda:
+            _check(lib().ctfmnmf_load_stft(self._h, c_void_p(X.data_ptr())), self._h)
+        else:
+            _check(lib().ctfmnmf_load_stft_host(self._h, c_void_p(X.data_ptr())), self._h)
+
+    def set_init(self, T0=None, V0=None):
+        import torch
+        if T0 is not None:
+            self._expect(T0, (self.N, self.F, self.B), torch.float32, cuda=True)
+        if V0 is not None:
+            self._expect(V0, (self.N, self.B, self.J), torch.float32, cuda=True)
+        _check(lib().ctfmnmf_set_init(self._h, _ptr(T0), _ptr(V0)), self._h)
+
+    def iterate(self, n_iter: int):
+        _check(lib().ctfmnmf_iterate(self._h, int(n_iter)), self._h)
+
+    # -- outputs
+    def cost(self) -> float:
+        out = c_double()
+        _check(lib().ctfmnmf_cost(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
+    def get_separated(self, out=None):
+        import torch
+        shape = (self.N, self.M, self.F, self.J)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        self._expect(out, shape, torch.complex64)
+        if out.is_cuda:
+            _check(lib().ctfmnmf_get_separated(self._h, c_void_p(out.data_ptr())), self._h)
+        else:
+            _check(lib().ctfmnmf_get_separated_host(self._h, c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def get_demixed(self):
+        import torch
+        out = torch.empty((self.M, self.F, self.J), dtype=torch.complex64, device="cuda")
+        _check(lib().ctfmnmf_get_demixed(self._h, c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def get_demix_matrix(self):
+        import torch
+        out = torch.empty((self.F, self.M, self.M), dtype=torch.complex64, device="cuda")
+        _check(lib().ctfmnmf_get_demix_matrix(self._h, c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def get_logdet(self):
+        import torch
+        out = torch.empty((self.F,), dtype=torch.float64, device="cuda")
+        _check(lib().ctfmnmf_get_logdet(self._h, c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def get_nmf(self):
+        import torch
+        T = torch.empty((self.N, self.F, self.B), dtype=torch.float32, device="cuda")
+        V = torch.empty((self.N, self.B, self.J), dtype=torch.float32, device="cuda")
+        _check(lib().ctfmnmf_get_nmf(self._h, c_void_p(T.data_ptr()), c_void_p(V.data_ptr())), self._h)
+        return T, V
+
+    # -- diagnostics
+    def time_phases(self, n_iter: int):
+        """Average device ms per launch of (bin phase, frame phase) over n_iter iterations."""
+        ms = (c_double * 2)()
+        _check(lib().ctfmnmf_time_phases(self._h, int(n_iter), ms), self._h)
+        return float(ms[0]), float(ms[1])
+
+    def launch_count(self) -> int:
+        out = ctypes.c_longlong()
+        _check(lib().ctfmnmf_get_launch_count(self._h, ctypes.byref(out)), self._h)
+        return int(out.value)
+
+    @staticmethod
+    def _expect(t, shape, dtype, cuda=None):
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+        if cuda and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")

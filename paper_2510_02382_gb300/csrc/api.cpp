@@ -1,0 +1,450 @@
+// Host side of the C ABI declared in include/ctfmnmf.h: argument checks, device
+// buffers, the launch sequence of one call and the CUDA-graph cache of ctfmnmf_iterate.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.cuh"
+
+using ctf::Shape;
+using ctf::State;
+
+struct ctfmnmf {
+    Shape s;
+    State d;
+    ctfmnmf_options opt;
+    int L;
+    int device;
+    cudaStream_t stream;        // user stream (nullptr = legacy default stream)
+    cudaStream_t capture;       // private stream used to capture the iteration graph
+    bool loaded;
+    cudaGraphExec_t graph;
+    int graph_iters;
+    double* host_cost;          // pinned one-double landing buffer
+    float2* sepbuf;             // device images for ctfmnmf_get_separated_host (lazy)
+    long long launches;         // kernels enqueued so far
+    char err[256];
+};
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+int fail(ctfmnmf* h, int code, const char* fmt, ...)
+{
+    char* buf = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail((h), CTFMNMF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void free_state(ctfmnmf* h)
+{
+    State& d = h->d;
+    void* ptrs[] = {d.Y, d.W, d.logdet, d.T, d.V, d.invlam, d.P, d.mupart, d.scale, d.flag,
+                    d.cost_part, d.cost_out, d.staging};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    memset(&h->d, 0, sizeof(h->d));
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    if (h->capture) cudaStreamDestroy(h->capture);
+    h->capture = nullptr;
+    if (h->host_cost) cudaFreeHost(h->host_cost);
+    h->host_cost = nullptr;
+    if (h->sepbuf) cudaFree(h->sepbuf);
+    h->sepbuf = nullptr;
+}
+
+int check_flag(ctfmnmf* h, int mask, const char* what)
+{
+    int flag = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&flag, h->d.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (flag & mask) {
+        CUDA_TRY(h, cudaMemsetAsync(h->d.flag, 0, sizeof(int), h->stream));
+        return fail(h, CTFMNMF_ENONFINITE, "%s holds NaN or Inf", what);
+    }
+    return CTFMNMF_OK;
+}
+
+// kernels per launcher: load 1, init_nmf 1, psd 1, bin/frame phase 1 each, finalize 2,
+// cost 2, separate 1, read-outs 1
+constexpr int kFinalizeKernels = 2;
+
+int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
+{
+    const int tap0 = h->opt.v_update == CTFMNMF_V_TAP0;
+    for (int t = 0; t < n_iter; ++t) {
+        CUDA_TRY(h, ctf::launch_bin_phase(h->s, h->d, tap0, st));
+        CUDA_TRY(h, ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, st));
+    }
+    CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, st));
+    return CTFMNMF_OK;
+}
+
+long long iteration_kernels(int n_iter) { return 2LL * n_iter + kFinalizeKernels; }
+
+}  // namespace
+
+extern "C" {
+
+void ctfmnmf_default_options(ctfmnmf_options* opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->v_update = CTFMNMF_V_ALL_TAPS;
+    opt->normalize = 1;
+    opt->use_graph = 1;
+}
+
+int ctfmnmf_create(int M, int N, int L, int B, int F, int J, ctfmnmf_t* out)
+{
+    ctfmnmf_dims d = {M, N, L, B, F, J};
+    return ctfmnmf_create_ex(&d, nullptr, nullptr, out);
+}
+
+int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_options* opt,
+                      ctfmnmf_t* out)
+{
+    g_create_err[0] = 0;
+    if (!out) return fail(nullptr, CTFMNMF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, CTFMNMF_EINVAL, "dims is NULL");
+    const int M = dims->M, N = dims->N, L = dims->L, B = dims->B, F = dims->F, J = dims->J;
+    if (M <= 0 || N <= 0 || L <= 0 || B <= 0 || F <= 0 || J <= 0)
+        return fail(nullptr, CTFMNMF_EINVAL, "every dimension must be positive");
+    if (N > M) return fail(nullptr, CTFMNMF_EINVAL, "N=%d sources exceed M=%d microphones", N, M);
+    if (M > CTFMNMF_MAX_M) return fail(nullptr, CTFMNMF_EINVAL, "M=%d exceeds %d", M, CTFMNMF_MAX_M);
+    if (B > CTFMNMF_MAX_B) return fail(nullptr, CTFMNMF_EINVAL, "B=%d exceeds %d", B, CTFMNMF_MAX_B);
+    ctfmnmf_options o;
+    ctfmnmf_default_options(&o);
+    if (opt) {
+        o = *opt;
+        if (o.v_update != CTFMNMF_V_ALL_TAPS && o.v_update != CTFMNMF_V_TAP0)
+            return fail(nullptr, CTFMNMF_EINVAL, "unknown v_update %d", o.v_update);
+        if ((o.normalize != 0 && o.normalize != 1) || (o.use_graph != 0 && o.use_graph != 1))
+            return fail(nullptr, CTFMNMF_EINVAL, "normalize and use_graph must be 0 or 1");
+        for (int k = 0; k < 5; ++k)
+            if (o.reserved[k]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
+    }
+    Shape s;
+    memset(&s, 0, sizeof(s));
+    s.M = M; s.N = N; s.B = B; s.F = F; s.J = J;
+    s.Jp = (J + 7) / 8 * 8;
+    int total = 0, lmax = 0;
+    for (int n = 0; n < N; ++n) {
+        const int t = Ln ? Ln[n] : M / N + (n < M % N ? 1 : 0);
+        if (t <= 0) return fail(nullptr, CTFMNMF_EINVAL, "tap count of source %d must be positive", n);
+        if (t > L) return fail(nullptr, CTFMNMF_EINVAL, "source %d has %d taps, more than L=%d", n, t, L);
+        s.Ln[n] = t;
+        s.row0[n] = total;
+        for (int l = 0; l < t && total + l < CTFMNMF_MAX_M; ++l) {
+            s.row_n[total + l] = n;
+            s.row_l[total + l] = l;
+        }
+        total += t;
+        if (t > lmax) lmax = t;
+    }
+    if (total != M) return fail(nullptr, CTFMNMF_EINVAL, "taps sum to %d, not M=%d", total, M);
+    if (J <= lmax) return fail(nullptr, CTFMNMF_EINVAL, "J=%d frames must exceed the longest tap count %d", J, lmax);
+    int fpt = 0, nt = 0;
+    if (!ctf::bin_phase_config(M, J, &fpt, &nt))
+        return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames is too long for M=%d in one thread block", J, M);
+
+    ctfmnmf* h = new (std::nothrow) ctfmnmf;
+    if (!h) return fail(nullptr, CTFMNMF_ENOMEM, "host allocation failed");
+    memset(h, 0, sizeof(*h));
+    h->s = s;
+    h->opt = o;
+    h->L = L;
+    cudaGetDevice(&h->device);
+
+    State& d = h->d;
+    const size_t MF = (size_t)M * F, FNJ = (size_t)F * N * s.Jp;
+    struct { void** p; size_t bytes; } allocs[] = {
+        {(void**)&d.Y, sizeof(float2) * MF * s.Jp},
+        {(void**)&d.W, sizeof(float2) * MF * M},
+        {(void**)&d.logdet, sizeof(double) * F},
+        {(void**)&d.T, sizeof(float) * (size_t)F * N * B},
+        {(void**)&d.V, sizeof(float) * (size_t)N * B * s.Jp},
+        {(void**)&d.invlam, sizeof(float) * FNJ},
+        {(void**)&d.P, sizeof(float) * FNJ},
+        {(void**)&d.mupart, sizeof(float) * MF},
+        {(void**)&d.scale, sizeof(float) * CTFMNMF_MAX_M},
+        {(void**)&d.flag, sizeof(int) * 4},
+        {(void**)&d.cost_part, sizeof(double) * F},
+        {(void**)&d.cost_out, sizeof(double)},
+    };
+    for (auto& a : allocs) {
+        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_state(h);
+            delete h;
+            return fail(nullptr, CTFMNMF_ENOMEM, "cudaMalloc of %zu bytes failed", a.bytes);
+        }
+    }
+    int rc = CTFMNMF_OK;
+    if (cudaMallocHost((void**)&h->host_cost, sizeof(double)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        rc = CTFMNMF_ECUDA;
+    }
+    if (rc == CTFMNMF_OK && (cudaMemset(d.flag, 0, sizeof(int) * 4) != cudaSuccess ||
+                             cudaMemset(d.P, 0, sizeof(float) * FNJ) != cudaSuccess ||
+                             cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
+        rc = CTFMNMF_ECUDA;
+    if (rc == CTFMNMF_OK && (ctf::configure_bin_phase(s) != cudaSuccess ||
+                             ctf::launch_init_nmf(s, d, nullptr, nullptr, 0, nullptr) != cudaSuccess ||
+                             ctf::launch_psd(s, d, nullptr) != cudaSuccess ||
+                             cudaDeviceSynchronize() != cudaSuccess))
+        rc = CTFMNMF_ECUDA;
+    if (rc != CTFMNMF_OK) {
+        const char* msg = cudaGetErrorString(cudaGetLastError());
+        free_state(h);
+        delete h;
+        return fail(nullptr, rc, "device set-up failed: %s", msg);
+    }
+    *out = h;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_destroy(ctfmnmf_t h)
+{
+    if (!h) return CTFMNMF_OK;
+    cudaStreamSynchronize(h->stream);
+    free_state(h);
+    delete h;
+    return CTFMNMF_OK;
+}
+
+const char* ctfmnmf_last_error(ctfmnmf_t h) { return h ? h->err : g_create_err; }
+
+int ctfmnmf_set_stream(ctfmnmf_t h, void* stream)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    h->stream = (cudaStream_t)stream;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_taps(ctfmnmf_t h, int* Ln)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!Ln) return fail(h, CTFMNMF_EINVAL, "Ln is NULL");
+    for (int n = 0; n < h->s.N; ++n) Ln[n] = h->s.Ln[n];
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_load_stft(ctfmnmf_t h, const void* X)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!X) return fail(h, CTFMNMF_EINVAL, "X is NULL");
+    h->err[0] = 0;
+    h->loaded = false;
+    CUDA_TRY(h, ctf::launch_load(h->s, h->d, (const float2*)X, h->stream));
+    CUDA_TRY(h, ctf::launch_psd(h->s, h->d, h->stream));
+    h->launches += 2;
+    int rc = check_flag(h, 1, "X");
+    if (rc != CTFMNMF_OK) return rc;
+    h->loaded = true;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_load_stft_host(ctfmnmf_t h, const void* X)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!X) return fail(h, CTFMNMF_EINVAL, "X is NULL");
+    const size_t bytes = sizeof(float2) * (size_t)h->s.M * h->s.F * h->s.J;
+    if (!h->d.staging) {
+        if (cudaMalloc((void**)&h->d.staging, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, CTFMNMF_ENOMEM, "cudaMalloc of %zu staging bytes failed", bytes);
+        }
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.staging, X, bytes, cudaMemcpyHostToDevice, h->stream));
+    return ctfmnmf_load_stft(h, h->d.staging);
+}
+
+int ctfmnmf_set_init(ctfmnmf_t h, const float* T0, const float* V0)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    h->err[0] = 0;
+    if (!T0 && !V0) return CTFMNMF_OK;
+    CUDA_TRY(h, ctf::launch_init_nmf(h->s, h->d, T0, V0, 0, h->stream));
+    CUDA_TRY(h, ctf::launch_psd(h->s, h->d, h->stream));
+    h->launches += 2;
+    return check_flag(h, 2, "T0/V0");
+}
+
+int ctfmnmf_iterate(ctfmnmf_t h, int n_iter)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (n_iter < 0) return fail(h, CTFMNMF_EINVAL, "n_iter=%d is negative", n_iter);
+    if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    h->err[0] = 0;
+    if (n_iter == 0) return CTFMNMF_OK;
+    if (!h->opt.use_graph) {
+        const int rc = enqueue_iterations(h, n_iter, h->stream);
+        if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter);
+        return rc;
+    }
+    if (!h->graph || h->graph_iters != n_iter) {
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(h, cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_iterations(h, n_iter, h->capture);
+        cudaError_t ec = cudaStreamEndCapture(h->capture, &g);
+        if (rc != CTFMNMF_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return fail(h, CTFMNMF_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) {
+            h->graph = nullptr;
+            return fail(h, CTFMNMF_ECUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+        }
+        h->graph_iters = n_iter;
+    }
+    CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+    h->launches += iteration_kernels(n_iter);
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_cost(ctfmnmf_t h, double* out)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!out) return fail(h, CTFMNMF_EINVAL, "out is NULL");
+    if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    CUDA_TRY(h, ctf::launch_cost(h->s, h->d, h->stream));
+    h->launches += 2;
+    CUDA_TRY(h, cudaMemcpyAsync(h->host_cost, h->d.cost_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    *out = *h->host_cost;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_separated(ctfmnmf_t h, void* C)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!C) return fail(h, CTFMNMF_EINVAL, "output is NULL");
+    if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    CUDA_TRY(h, ctf::launch_separate(h->s, h->d, (float2*)C, h->stream));
+    h->launches += 1;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_separated_host(ctfmnmf_t h, void* C)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!C) return fail(h, CTFMNMF_EINVAL, "output is NULL");
+    if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    const size_t bytes = sizeof(float2) * (size_t)h->s.N * h->s.M * h->s.F * h->s.J;
+    if (!h->sepbuf) {
+        if (cudaMalloc((void**)&h->sepbuf, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, CTFMNMF_ENOMEM, "cudaMalloc of %zu output bytes failed", bytes);
+        }
+    }
+    CUDA_TRY(h, ctf::launch_separate(h->s, h->d, h->sepbuf, h->stream));
+    h->launches += 1;
+    CUDA_TRY(h, cudaMemcpyAsync(C, h->sepbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_demixed(ctfmnmf_t h, void* Y)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!Y) return fail(h, CTFMNMF_EINVAL, "output is NULL");
+    CUDA_TRY(h, ctf::launch_get_demixed(h->s, h->d, (float2*)Y, h->stream));
+    h->launches += 1;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_demix_matrix(ctfmnmf_t h, void* W)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!W) return fail(h, CTFMNMF_EINVAL, "output is NULL");
+    CUDA_TRY(h, cudaMemcpyAsync(W, h->d.W, sizeof(float2) * (size_t)h->s.F * h->s.M * h->s.M,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_logdet(ctfmnmf_t h, double* logdet)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!logdet) return fail(h, CTFMNMF_EINVAL, "output is NULL");
+    CUDA_TRY(h, cudaMemcpyAsync(logdet, h->d.logdet, sizeof(double) * h->s.F, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_nmf(ctfmnmf_t h, float* T, float* V)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!T && !V) return CTFMNMF_OK;
+    CUDA_TRY(h, ctf::launch_get_nmf(h->s, h->d, T, V, h->stream));
+    h->launches += 1;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!ms || n_iter < 1) return fail(h, CTFMNMF_EINVAL, "need n_iter >= 1 and an output");
+    if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    const int tap0 = h->opt.v_update == CTFMNMF_V_TAP0;
+    cudaEvent_t ev[4];
+    for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+    double tot[2] = {0.0, 0.0};
+    int rc = CTFMNMF_OK;
+    for (int t = 0; t < n_iter && rc == CTFMNMF_OK; ++t) {
+        cudaError_t e = cudaEventRecord(ev[0], h->stream);
+        if (e == cudaSuccess) e = ctf::launch_bin_phase(h->s, h->d, tap0, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+        if (e == cudaSuccess) e = ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        float a = 0.f, b = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2], ev[3]);
+        if (e != cudaSuccess) rc = fail(h, CTFMNMF_ECUDA, "phase timing: %s", cudaGetErrorString(e));
+        tot[0] += a;
+        tot[1] += b;
+    }
+    if (rc == CTFMNMF_OK && ctf::launch_finalize(h->s, h->d, h->stream) != cudaSuccess)
+        rc = fail(h, CTFMNMF_ECUDA, "finalize launch failed");
+    if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter);
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc != CTFMNMF_OK) return rc;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    ms[0] = tot[0] / n_iter;
+    ms[1] = tot[1] / n_iter;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_launch_count(ctfmnmf_t h, long long* count)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!count) return fail(h, CTFMNMF_EINVAL, "count is NULL");
+    *count = h->launches;
+    return CTFMNMF_OK;
+}
+
+}  // extern "C"

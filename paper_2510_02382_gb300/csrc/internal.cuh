@@ -1,0 +1,88 @@
+// Internal definitions shared by the CUDA translation units of libctfmnmf.
+//
+// Device data layout (one mixture, all resident in HBM):
+//   Y      [F][M][Jp]  complex64  demixed extended rows, bin-major: one bin is one
+//                                 contiguous block of M*Jp*8 bytes (Jp = J rounded up to 4)
+//   W      [F][M][M]   complex64  row r of W_i holds w_r^H
+//   logdet [F]         float64    log|det W_i|, tracked by the determinant lemma
+//   T      [F][N][B]   float32    bases, bin-major (the API shape is [N][F][B])
+//   V      [N][B][Jp]  float32    activations (padding frames are 0)
+//   invlam [F][N][Jp]  float32    1/lambda_{n,i,j} for the current T, V (padding 0)
+//   P      [F][N][Jp]  float32    delayed row power feeding the activation update
+//   mupart [F][M]      float32    per-bin row power sums feeding the normalisation
+//   scale  [M]         float32    pending normalisation 1/mu_r not yet applied to Y, W, T
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ctfmnmf.h"
+
+namespace ctf {
+
+constexpr float kFloorNmf = 1e-12f;   // floor of T and V after each multiplicative update
+constexpr float kFloorPsd = 1e-18f;   // floor of lambda where it is formed
+
+struct Shape {
+    int M, N, B, F, J, Jp;
+    int Ln[CTFMNMF_MAX_M];
+    int row_n[CTFMNMF_MAX_M];   // extended row r -> source n
+    int row_l[CTFMNMF_MAX_M];   // extended row r -> tap l
+    int row0[CTFMNMF_MAX_M];    // source n -> its tap-0 row
+};
+
+struct State {
+    float2* Y;
+    float2* W;
+    double* logdet;
+    float* T;
+    float* V;
+    float* invlam;
+    float* P;
+    float* mupart;
+    float* scale;
+    int* flag;          // [0]: non-finite input seen
+    double* cost_part;  // [F] per-bin cost
+    double* cost_out;   // [1]
+    float2* staging;    // host-loaded STFT staging [M][F][J]
+};
+
+// Launchers (host functions; each enqueues its kernels on `st` and returns the
+// cudaGetLastError() of the launch).
+cudaError_t launch_load(const Shape& s, const State& d, const float2* X, cudaStream_t st);
+cudaError_t launch_init_nmf(const Shape& s, const State& d, const float* T0, const float* V0,
+                            uint64_t seed, cudaStream_t st);
+cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st);
+cudaError_t configure_bin_phase(const Shape& s);
+cudaError_t launch_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
+cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
+                               cudaStream_t st);
+cudaError_t launch_finalize(const Shape& s, const State& d, cudaStream_t st);
+cudaError_t launch_cost(const Shape& s, const State& d, cudaStream_t st);
+cudaError_t launch_separate(const Shape& s, const State& d, float2* out, cudaStream_t st);
+cudaError_t launch_get_demixed(const Shape& s, const State& d, float2* out, cudaStream_t st);
+cudaError_t launch_get_nmf(const Shape& s, const State& d, float* T, float* V, cudaStream_t st);
+
+// Frames per thread / threads per block chosen for the bin phase; false if unsupported.
+bool bin_phase_config(int M, int J, int* fpt, int* threads);
+size_t bin_phase_smem(const Shape& s);
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {   // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace ctf

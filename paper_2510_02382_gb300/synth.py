@@ -156,3 +156,25 @@ def random_case(seed: int, M: int, N: int, F: int, J: int, B: int, Ln=None, L=No
     L = L if L is not None else max(Ln)
     return make_mixture(MixSpec("rand", N=N, M=M, L=L, tau=2.0, F=F, J=J, B=B, iters=1,
                                 seed=seed, Ln=tuple(Ln)))
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 (Steele, Lea, Flood 2014; constants of Vigna's splitmix64.c), uint64 wrap-around."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)).astype(np.uint64)
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)).astype(np.uint64)
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)).astype(np.uint64)
+        return z ^ (z >> np.uint64(31))
+
+
+def library_default_factors(N: int, F: int, B: int, J: int, seed: int = 0):
+    """The library's default NMF init: element e of T0 [N][F][B] is 0.1 + 0.9 u(2e), of
+    V0 [N][B][J] 0.1 + 0.9 u(2e+1), u(c) = top 24 bits of splitmix64(seed*2^32 + c) / 2^24."""
+    base = np.uint64(seed) << np.uint64(32)
+
+    def vals(count, odd):
+        c = np.arange(count, dtype=np.uint64) * np.uint64(2) + np.uint64(odd)
+        u = (splitmix64(base + c) >> np.uint64(40)).astype(np.float64) / 16777216.0
+        return (0.1 + 0.9 * u).astype(np.float32)
+
+    return vals(N * F * B, 0).reshape(N, F, B), vals(N * B * J, 1).reshape(N, B, J)

@@ -1,0 +1,47 @@
+"""Shared helpers of the GPU tests: run the CUDA library and the oracle on one mixture."""
+import numpy as np
+
+from oracle import ctfmnmf_oracle as O
+
+
+def run_gpu(mix, n_iter, v_mode="all_taps", normalize=True, use_graph=True, set_init=True):
+    import torch
+    from paper_2510_02382_gb300.api import CTFMNMF
+    sp = mix.spec
+    s = CTFMNMF(sp.M, sp.N, max(mix.Ln), sp.B, sp.F, sp.J, Ln=mix.Ln, v_update=v_mode,
+                normalize=normalize, use_graph=use_graph)
+    X = torch.from_numpy(mix.X).cuda()
+    s.load_stft(X)
+    if set_init:
+        s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+    s.iterate(n_iter)
+    out = {
+        "y": s.get_demixed().cpu().numpy(),
+        "W": s.get_demix_matrix().cpu().numpy(),
+        "logdet": s.get_logdet().cpu().numpy(),
+        "cost": s.cost(),
+        "images": s.get_separated().cpu().numpy(),
+    }
+    T, V = s.get_nmf()
+    out["T"], out["V"] = T.cpu().numpy(), V.cpu().numpy()
+    s.close()
+    return out
+
+
+def run_oracle(mix, n_iter, v_mode="all_taps", normalize=True, T0=None, V0=None):
+    T0 = mix.T0 if T0 is None else T0
+    V0 = mix.V0 if V0 is None else V0
+    ref = O.run(mix.X, mix.Ln, T0, V0, n_iter, v_mode=v_mode, normalize=normalize)
+    ref["images"] = O.source_images(ref["W"], ref["y"], mix.Ln)
+    return ref
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def cost_close(c_gpu, c_ref, tol, F, J, M):
+    """Cost agreement scaled by max(|L_ref|, F*J*M): the cost can sit near zero, where a
+    purely relative test is ill-conditioned; F*J*M is the number of terms of Eq. 5."""
+    scale = max(abs(c_ref), float(F) * J * M)
+    return abs(c_gpu - c_ref) <= tol * scale, abs(c_gpu - c_ref) / scale

@@ -32,7 +32,7 @@ def _small(seed=0, M=3, N=2, F=5, J=24, B=3, Ln=None):
     return mix, x, W, b, v
 
 
-# --- ISS step: closed form (Eq. 13) vs brute-force minimisation of the ISS sub-objective (Eq. 10)
+# --- ISS step: closed form (Eq. 16) vs brute-force minimisation of the ISS sub-objective (Eq. 12)
 
 @pytest.mark.parametrize("M", [2, 3, 4])
 @pytest.mark.parametrize("seed", [0, 1])
@@ -73,7 +73,7 @@ def test_iss_closed_form_is_the_minimiser(M, seed):
 
 
 def test_printed_conjugate_numerator_is_not_the_minimiser():
-    """The numerator printed in Eq. 13 is the conjugate of the minimiser; on complex data
+    """The numerator printed in Eq. 16 is the conjugate of the minimiser; on complex data
     it gives a strictly larger objective, so the oracle must not use it."""
     rng = np.random.default_rng(7)
     M = 3
@@ -104,7 +104,7 @@ def test_determinant_lemma_tracks_logdet():
     assert np.max(np.abs(tracked - O.logabsdet(W2))) < 1e-10
 
 
-# --- Monotonicity: auxiliary function (Eq. 6) per row step; NLL (Eq. 5) per sub-step
+# --- Monotonicity: auxiliary function (Eq. 7) per row step; NLL (Eq. 5) per sub-step
 
 def test_aux_nonincreasing_each_row_step():
     rng = np.random.default_rng(5)
@@ -145,7 +145,7 @@ def test_nll_nonincreasing_each_substep(Ln, M, N):
         prev = O.nll(y, O.psd(b, v), W, Ln)
 
 
-# --- The cost of Eq. 5 equals J * (aux of Eq. 6 with Q of Eq. 7) + sum of log lambda
+# --- The cost of Eq. 5 equals J * (aux of Eq. 7 with Q of Eq. 8) + sum of log lambda
 
 def test_cost_equals_auxiliary_form():
     Ln = (2, 1)
@@ -160,7 +160,7 @@ def test_cost_equals_auxiliary_form():
     assert abs(O.nll(y, lam, W, Ln) - (J * np.sum(O.aux_value(W, Q)) + logs)) < 1e-9 * J
 
 
-# --- MU rules (Eqs. 14-15): fixed point and gradient split
+# --- MU rules (Eqs. 17-18): fixed point and gradient split
 
 def _matched_y(lam, Ln, rng):
     """y with |y_{(n,l),i,j}|^2 = lambda_{n,i,j-l} exactly on the unmasked frames."""
@@ -228,7 +228,7 @@ def test_nmf_factors_stay_positive():
     assert np.all(np.isfinite(out["y"]))
 
 
-# --- Normalisation (Eqs. 16-18)
+# --- Normalisation (Eqs. 19-21)
 
 def test_normalisation_gives_unit_row_power_and_keeps_y_equal_wx():
     Ln = (2, 1)
@@ -242,7 +242,7 @@ def test_normalisation_gives_unit_row_power_and_keeps_y_equal_wx():
     assert np.allclose(b2[0], b[0] / mu[0] ** 2) and np.allclose(b2[1], b[1] / mu[2] ** 2)
 
 
-# --- Source images (Eq. 20): projection-back, sum to the mixture, literal MWF
+# --- Source images (Eqs. 23-24): projection-back, sum to the mixture, literal MWF
 
 def test_images_sum_to_mixture_and_equal_literal_mwf():
     Ln = (2, 1)
@@ -257,7 +257,7 @@ def test_images_sum_to_mixture_and_equal_literal_mwf():
     assert np.max(np.abs(c[..., lmax:] - c_mwf[..., lmax:])) < 1e-9
 
 
-# --- IP (Eqs. 8-9) and the ISS/IP fixed points
+# --- IP (Eqs. 9-10) and the ISS/IP fixed points
 
 def test_ip_last_row_satisfies_head():
     rng = np.random.default_rng(21)

@@ -1,0 +1,217 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle, on seeded inputs.
+
+Tolerances (complex64 / FP32 on the GPU, FP64 in the oracle):
+  * demixed rows Y after 1 iteration: 1e-4 relative Frobenius;
+  * cost (Eq. 5) after 10 iterations: 1e-5, after 100 iterations: 1e-3, both relative to
+    max(|cost|, F*J*M) (the number of terms of the sum);
+  * W, T, V, log|det W| and the images after 1 iteration: 1e-4 relative Frobenius.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_02382_gb300 import synth
+
+from gpu_helpers import cost_close, rel_fro, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_state(g, r, mix, tol=1e-4):
+    assert rel_fro(g["y"], r["y"]) < tol, rel_fro(g["y"], r["y"])
+    assert rel_fro(g["W"], r["W"]) < tol, rel_fro(g["W"], r["W"])
+    assert rel_fro(g["T"], r["b"]) < tol, rel_fro(g["T"], r["b"])
+    assert rel_fro(g["V"], r["v"]) < tol, rel_fro(g["V"], r["v"])
+    assert np.max(np.abs(g["logdet"] - r["logdet"])) < 1e-4 * max(1.0, np.max(np.abs(r["logdet"])))
+    assert rel_fro(g["images"], r["images"]) < tol, rel_fro(g["images"], r["images"])
+
+
+# shapes that span several warps, ragged J tails, each frames-per-thread branch and M = 2..8
+SHAPES = [
+    # (M, N, Ln, F, J, B)
+    (3, 2, (2, 1), 7, 37, 4),
+    (3, 2, (2, 1), 5, 301, 10),
+    (2, 2, (1, 1), 6, 513, 3),
+    (4, 3, (2, 1, 1), 4, 1001, 16),
+    (4, 2, (2, 2), 3, 2049, 5),
+    (3, 1, (3,), 3, 200, 2),
+    (5, 2, (3, 2), 4, 260, 6),
+    (6, 2, (3, 3), 3, 120, 3),
+    (7, 3, (3, 2, 2), 3, 90, 8),
+    (8, 2, (4, 4), 4, 501, 3),
+    (4, 2, (2, 2), 2, 3001, 32),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"M{s[0]}N{s[1]}F{s[3]}J{s[4]}B{s[5]}")
+def test_one_iteration_matches_oracle(shape):
+    M, N, Ln, F, J, B = shape
+    mix = synth.random_case(1000 + M * 7 + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+    g = run_gpu(mix, 1)
+    r = run_oracle(mix, 1)
+    _check_state(g, r, mix)
+    ok, err = cost_close(g["cost"], r["cost"], 1e-5, F, J, M)
+    assert ok, err
+
+
+@pytest.mark.parametrize("shape", SHAPES[:5], ids=lambda s: f"M{s[0]}F{s[3]}J{s[4]}")
+def test_ten_iterations_cost(shape):
+    M, N, Ln, F, J, B = shape
+    mix = synth.random_case(2000 + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+    g = run_gpu(mix, 10)
+    r = run_oracle(mix, 10)
+    ok, err = cost_close(g["cost"], r["cost"], 1e-5, F, J, M)
+    assert ok, err
+
+
+def test_c1_workload_10_iterations():
+    """The small single-mixture workload: N=2, M=3, F=129, J=256, B=4, 10 iterations."""
+    mix = synth.make_mixture(synth.CONFIGS["C1"])
+    sp = mix.spec
+    g1, r1 = run_gpu(mix, 1), run_oracle(mix, 1)
+    assert rel_fro(g1["y"], r1["y"]) < 1e-4
+    g, r = run_gpu(mix, 10), run_oracle(mix, 10)
+    ok, err = cost_close(g["cost"], r["cost"], 1e-5, sp.F, sp.J, sp.M)
+    assert ok, err
+
+
+def test_tap0_activation_update_and_no_normalisation():
+    mix = synth.random_case(77, M=4, N=2, F=5, J=300, B=4, Ln=(2, 2))
+    for v_mode, norm in [("tap0", True), ("all_taps", False), ("tap0", False)]:
+        g = run_gpu(mix, 3, v_mode=v_mode, normalize=norm)
+        r = run_oracle(mix, 3, v_mode=v_mode, normalize=norm)
+        assert rel_fro(g["y"], r["y"]) < 1e-4, (v_mode, norm)
+        ok, err = cost_close(g["cost"], r["cost"], 1e-5, 5, 300, 4)
+        assert ok, (v_mode, norm, err)
+
+
+def test_graph_and_stream_launches_agree():
+    mix = synth.random_case(5, M=3, N=2, F=6, J=100, B=4, Ln=(2, 1))
+    a = run_gpu(mix, 4, use_graph=True)
+    b = run_gpu(mix, 4, use_graph=False)
+    assert np.array_equal(a["y"], b["y"]) and a["cost"] == b["cost"]
+
+
+def test_repeated_iterate_calls_compose():
+    """iterate(2) twice equals iterate(4): the normalisation carried between calls is exact."""
+    import torch
+    from paper_2510_02382_gb300.api import CTFMNMF
+    mix = synth.random_case(9, M=3, N=2, F=4, J=64, B=3, Ln=(2, 1))
+    sp = mix.spec
+    outs = []
+    for split in [(4,), (2, 2), (1, 3)]:
+        s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln)
+        s.load_stft(torch.from_numpy(mix.X).cuda())
+        s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+        for k in split:
+            s.iterate(k)
+        outs.append((s.get_demixed().cpu().numpy(), s.cost()))
+        s.close()
+    for y, c in outs[1:]:
+        assert rel_fro(y, outs[0][0]) < 1e-6 and abs(c - outs[0][1]) <= 1e-6 * abs(outs[0][1])
+
+
+def test_default_init_matches_published_generator():
+    import torch
+    from paper_2510_02382_gb300.api import CTFMNMF
+    s = CTFMNMF(3, 2, 2, 5, 7, 45)
+    T, V = s.get_nmf()
+    T0, V0 = synth.library_default_factors(2, 7, 5, 45)
+    assert np.array_equal(T.cpu().numpy(), T0) and np.array_equal(V.cpu().numpy(), V0)
+    mix = synth.random_case(3, M=3, N=2, F=7, J=45, B=5, Ln=(2, 1))
+    s.load_stft(torch.from_numpy(mix.X).cuda())
+    s.iterate(2)
+    r = run_oracle(mix, 2, T0=T0, V0=V0)
+    assert rel_fro(s.get_demixed().cpu().numpy(), r["y"]) < 1e-4
+    s.close()
+
+
+def test_zero_energy_bin_and_minimum_frames():
+    mix = synth.random_case(21, M=3, N=2, F=4, J=3, B=2, Ln=(2, 1))   # J = max taps + 1
+    g, r = run_gpu(mix, 2), run_oracle(mix, 2)
+    assert rel_fro(g["y"], r["y"]) < 1e-4
+    mix = synth.random_case(22, M=3, N=2, F=5, J=40, B=3, Ln=(2, 1))
+    mix.X[:, 2, :] = 0
+    g, r = run_gpu(mix, 3), run_oracle(mix, 3)
+    assert np.all(np.isfinite(g["y"])) and np.isfinite(g["cost"])
+    assert rel_fro(g["y"], r["y"]) < 1e-4
+    ok, err = cost_close(g["cost"], r["cost"], 1e-5, 5, 40, 3)
+    assert ok, err
+
+
+def test_single_bin_single_source():
+    mix = synth.random_case(23, M=2, N=1, F=1, J=50, B=2, Ln=(2,))
+    g, r = run_gpu(mix, 2), run_oracle(mix, 2)
+    assert rel_fro(g["y"], r["y"]) < 1e-4
+
+
+def test_nonfinite_input_is_rejected():
+    import torch
+    from paper_2510_02382_gb300.api import CTFMNMF, CtfMnmfError
+    s = CTFMNMF(3, 2, 2, 3, 4, 16)
+    X = torch.zeros((3, 4, 16), dtype=torch.complex64, device="cuda")
+    X[1, 2, 5] = complex(float("nan"), 0.0)
+    with pytest.raises(CtfMnmfError) as e:
+        s.load_stft(X)
+    assert e.value.name == "ENONFINITE"
+    with pytest.raises(CtfMnmfError) as e:
+        s.iterate(1)
+    assert e.value.name == "ESTATE"
+    T0 = torch.ones((2, 4, 3), device="cuda")
+    T0[0, 0, 0] = float("inf")
+    with pytest.raises(CtfMnmfError) as e:
+        s.set_init(T0, None)
+    assert e.value.name == "ENONFINITE"
+    s.load_stft(torch.ones((3, 4, 16), dtype=torch.complex64, device="cuda"))
+    s.close()
+
+
+def test_host_buffers_match_device_buffers():
+    import torch
+    from paper_2510_02382_gb300.api import CTFMNMF
+    mix = synth.random_case(31, M=3, N=2, F=6, J=80, B=3, Ln=(2, 1))
+    sp = mix.spec
+    res = []
+    for host in (False, True):
+        s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln)
+        X = torch.from_numpy(mix.X)
+        s.load_stft(X if host else X.cuda())
+        s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+        s.iterate(3)
+        out = torch.empty((sp.N, sp.M, sp.F, sp.J), dtype=torch.complex64)
+        if host:
+            out = out.pin_memory()
+            s.get_separated(out)
+        else:
+            out = s.get_separated().cpu()
+        res.append(out.numpy())
+        s.close()
+    assert np.array_equal(res[0], res[1])
+
+
+# ---- full-size workloads (the benchmark's launch configuration)
+
+def test_c2_full_size_1_and_10_iterations():
+    mix = synth.make_mixture(synth.CONFIGS["C2"])
+    sp = mix.spec
+    g, r = run_gpu(mix, 1), run_oracle(mix, 1)
+    assert rel_fro(g["y"], r["y"]) < 1e-4, rel_fro(g["y"], r["y"])
+    g, r = run_gpu(mix, 10), run_oracle(mix, 10)
+    ok, err = cost_close(g["cost"], r["cost"], 1e-5, sp.F, sp.J, sp.M)
+    assert ok, err
+
+
+def test_c2_full_size_100_iterations_cost():
+    mix = synth.make_mixture(synth.CONFIGS["C2"])
+    sp = mix.spec
+    g, r = run_gpu(mix, 100), run_oracle(mix, 100)
+    ok, err = cost_close(g["cost"], r["cost"], 1e-3, sp.F, sp.J, sp.M)
+    assert ok, err
+
+
+def test_c3_full_size_1_iteration():
+    mix = synth.make_mixture(synth.CONFIGS["C3"])
+    g, r = run_gpu(mix, 1), run_oracle(mix, 1)
+    assert rel_fro(g["y"], r["y"]) < 1e-4, rel_fro(g["y"], r["y"])
+    sp = mix.spec
+    ok, err = cost_close(g["cost"], r["cost"], 1e-5, sp.F, sp.J, sp.M)
+    assert ok, err
