@@ -84,7 +84,7 @@ void ctfmnmf_default_options(ctfmnmf_options* opt);
  * (the square model of Sec. II; M=4,6,8 with N=2 gives the paper's Table I).
  * EINVAL if a dimension is <= 0, N > M, M > CTFMNMF_MAX_M, B > CTFMNMF_MAX_B,
  * a derived L_n exceeds L, J <= max L_n, or out is NULL.
- * EUNSUPPORTED if J exceeds 4096 (M <= 4) or 2048 (M = 5..8).
+ * EUNSUPPORTED if J exceeds 4096 (M <= 4) or 1024 (M = 5..8).
  * On success *out receives the handle; on failure *out is set to NULL.
  */
 int ctfmnmf_create(int M, int N, int L, int B, int F, int J, ctfmnmf_t* out);

@@ -205,6 +205,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
                              cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
         rc = CTFMNMF_ECUDA;
     if (rc == CTFMNMF_OK && (ctf::configure_bin_phase(s) != cudaSuccess ||
+                             ctf::configure_frame_phase() != cudaSuccess ||
                              ctf::launch_init_nmf(s, d, nullptr, nullptr, 0, nullptr) != cudaSuccess ||
                              ctf::launch_psd(s, d, nullptr) != cudaSuccess ||
                              cudaDeviceSynchronize() != cudaSuccess))

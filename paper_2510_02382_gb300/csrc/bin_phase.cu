@@ -20,46 +20,51 @@
 
 namespace ctf {
 
-template <int M, int FPT>
-__global__ void __launch_bounds__(512)
+constexpr int kLPad = 8;   // zero frames in front of each staged 1/lambda row (taps <= 8)
+
+template <int M, int FPT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 bin_phase_kernel(const Shape s, const State d, const int v_tap0)
 {
-    extern __shared__ float smem[];
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
     const int i = blockIdx.x;
     const int NT = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
     const int J = s.J, Jp = s.Jp, N = s.N, B = s.B;
+    const int LR = kLPad + Jp;           // staged row length
 
-    float* sq = smem;                    // [M][Jp]  |y_r(j)|^2 after the sweep
-    float* Aw = sq + M * Jp;             // [N][Jp]  P_n(j) / lambda^2
-    float* Cw = Aw + N * Jp;             // [N][Jp]  c_n(j) / lambda
-    float* red = Cw + N * Jp;            // [2][NW][3M] per-warp partial sums
+    float* ils = smem;                   // [N][LR] 1/lambda_{n,i,j} at kLPad + j, zeros in front;
+                                         //         reused for P_n(j)/lambda^2 after the sweep
+    float* Cw = ils + N * LR;            // [N][Jp]  c_n(j) / lambda
+    float* sq = Cw + N * Jp;             // [M][Jp]  |y_r(j)|^2 after the sweep
+    float* red = sq + M * Jp;            // [2][NW][3M] per-warp partial sums
+
+    // ---- stage 1/lambda of this bin (float4, coalesced; the front pad is zero)
+    {
+        const float4* src = reinterpret_cast<const float4*>(d.invlam + (size_t)i * N * Jp);
+        const int LR4 = LR >> 2, J4 = Jp >> 2, P4 = kLPad >> 2;
+        for (int e = tid; e < N * LR4; e += NT) {
+            const int n = e / LR4, o = e - n * LR4;
+            smem4[e] = (o < P4) ? make_float4(0.f, 0.f, 0.f, 0.f) : src[(size_t)n * J4 + o - P4];
+        }
+    }
 
     float scl[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) scl[r] = d.scale[r];
 
-    // ---- load y (with the pending scale) and the delayed weights
+    // ---- load y with the pending scale (padding frames are zero in memory)
     const float2* Yb = d.Y + (size_t)i * M * Jp;
-    const float* il = d.invlam + (size_t)i * N * Jp;
     float2 y[M][FPT];
-    float phi[M][FPT];
 #pragma unroll
     for (int r = 0; r < M; ++r) {
-        const int n = s.row_n[r], l = s.row_l[r];
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const int j = tid + f * NT;
             float2 v = make_float2(0.f, 0.f);
-            float w = 0.f;
-            if (j < J) {
-                v = Yb[(size_t)r * Jp + j];
-                v.x *= scl[r];
-                v.y *= scl[r];
-                if (j >= l) w = il[(size_t)n * Jp + j - l];
-            }
-            y[r][f] = v;
-            phi[r][f] = w;
+            if (j < Jp) v = Yb[(size_t)r * Jp + j];
+            y[r][f] = make_float2(v.x * scl[r], v.y * scl[r]);
         }
     }
 
@@ -68,12 +73,14 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
     if (tid < M) {
 #pragma unroll
         for (int p = 0; p < M; ++p) {
-            float2 w = d.W[((size_t)i * M + p) * M + tid];
+            const float2 w = d.W[((size_t)i * M + p) * M + tid];
             wcol[p] = make_float2(w.x * scl[p], w.y * scl[p]);
         }
     }
+    __syncthreads();
 
-    double dlog = 0.0;
+    double qprod = 1.0;                  // product of the q_r of the sweep (thread 0)
+    const float invJ = 1.0f / (float)J;
     // ---- ISS sweep
 #pragma unroll
     for (int r = 0; r < M; ++r) {
@@ -82,15 +89,17 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
         for (int k = 0; k < 3 * M; ++k) acc[k] = 0.f;
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
+            const int j = min(tid + f * NT, Jp - 1);   // frames past Jp hold y = 0
             const float2 yr = y[r][f];
             const float pr = abs2(yr);
 #pragma unroll
             for (int p = 0; p < M; ++p) {
-                acc[p] = fmaf(phi[p][f], pr, acc[p]);
+                const float ph = ils[s.row_n[p] * LR + kLPad + j - s.row_l[p]];
+                acc[p] = fmaf(ph, pr, acc[p]);
                 if (p != r) {
                     const float2 c = cmul_conj(y[p][f], yr);
-                    acc[M + 2 * p] = fmaf(phi[p][f], c.x, acc[M + 2 * p]);
-                    acc[M + 2 * p + 1] = fmaf(phi[p][f], c.y, acc[M + 2 * p + 1]);
+                    acc[M + 2 * p] = fmaf(ph, c.x, acc[M + 2 * p]);
+                    acc[M + 2 * p + 1] = fmaf(ph, c.y, acc[M + 2 * p + 1]);
                 }
             }
         }
@@ -121,12 +130,14 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
                 z[p] = make_float2(tot[M + 2 * p] * inv, tot[M + 2 * p + 1] * inv);
             }
         }
-        const double q = (double)tot[r] / (double)J;
+        // q = (1/J) sum_j phi_r |y_r|^2; 1 - z_r = q^{-1/2} (FP32 reciprocal square root with
+        // one Newton step); log|1 - z_r| is accumulated in FP64 through the product of q.
+        const float q = tot[r] * invJ;
         float sc = 1.0f;
-        if (q > 0.0) {
-            const double scd = 1.0 / sqrt(q);
-            sc = (float)scd;
-            dlog += -0.5 * log(q);
+        if (q > 0.f) {
+            const float r0 = rsqrtf(q);
+            sc = r0 * fmaf(-0.5f * q * r0, r0, 1.5f);
+            if (tid == 0) qprod *= (double)q;
         }
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
@@ -151,7 +162,7 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
         }
     }
 
-    // ---- store y, W, log|det W|; stage |y|^2
+    // ---- store y and W; stage |y|^2
     float2* Yo = d.Y + (size_t)i * M * Jp;
 #pragma unroll
     for (int r = 0; r < M; ++r) {
@@ -168,15 +179,10 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
 #pragma unroll
         for (int p = 0; p < M; ++p) d.W[((size_t)i * M + p) * M + tid] = wcol[p];
     }
-    if (tid == 0) {
-        double ls = 0.0;
-#pragma unroll
-        for (int r = 0; r < M; ++r) ls += log((double)scl[r]);
-        d.logdet[i] += ls + dlog;
-    }
     __syncthreads();
 
-    // ---- delayed power and the basis-update weights at this thread's frames
+    // ---- delayed power and the basis-update weights at this thread's frames; the
+    //      P/lambda^2 weight overwrites this thread's own 1/lambda entry in place
     float* Pout = d.P + (size_t)i * N * Jp;
 #pragma unroll
     for (int p = 0; p < M; ++p) {
@@ -194,27 +200,42 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
                     cnt += 1.f;
                 }
             }
-            const float w = phi[p][f];          // 1/lambda_{n,i,j} (tap 0 has no delay)
-            Aw[n * Jp + j] = P * w * w;
+            float* wp = ils + n * LR + kLPad + j;
+            const float w = *wp;                // 1/lambda_{n,i,j} (zero past J)
+            *wp = P * w * w;
             Cw[n * Jp + j] = cnt * w;
             Pout[(size_t)n * Jp + j] = v_tap0 ? sq[p * Jp + j] : P;
         }
     }
     __syncthreads();
 
-    // ---- basis MU (one warp per (n,k)) and per-row power sums for mu
+    // ---- basis MU: one warp per (n,k); V rows through the L1 (shared by the CTAs of an
+    //      SM), float4, a batch of independent loads per lane before the FMAs
     const int npairs = N * B;
+    const int J4 = Jp >> 2;
     for (int t = warp; t < npairs + M; t += NW) {
         if (t < npairs) {
             const int n = t / B, k = t - n * B;
-            const float* Vk = d.V + (size_t)(n * B + k) * Jp;
-            const float* An = Aw + n * Jp;
-            const float* Cn = Cw + n * Jp;
+            const float4* V4 = reinterpret_cast<const float4*>(d.V + (size_t)(n * B + k) * Jp);
+            const float4* A4 = reinterpret_cast<const float4*>(ils + n * LR + kLPad);
+            const float4* C4 = reinterpret_cast<const float4*>(Cw + n * Jp);
             float a = 0.f, c = 0.f;
-            for (int j = lane; j < J; j += 32) {
-                const float v = Vk[j];
-                a = fmaf(v, An[j], a);
-                c = fmaf(v, Cn[j], c);
+            for (int base = lane; base < J4; base += 32 * 8) {
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = base + 32 * u;
+                    v[u] = q < J4 ? __ldg(V4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = base + 32 * u;
+                    if (q < J4) {
+                        const float4 x = A4[q], cc = C4[q];
+                        a = fmaf(v[u].x, x.x, fmaf(v[u].y, x.y, fmaf(v[u].z, x.z, fmaf(v[u].w, x.w, a))));
+                        c = fmaf(v[u].x, cc.x, fmaf(v[u].y, cc.y, fmaf(v[u].z, cc.z, fmaf(v[u].w, cc.w, c))));
+                    }
+                }
             }
             a = warp_sum(a);
             c = warp_sum(c);
@@ -227,30 +248,40 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
             }
         } else {
             const int r = t - npairs;
+            const float4* S4 = reinterpret_cast<const float4*>(sq + r * Jp);
             float a = 0.f;
-            for (int j = lane; j < J; j += 32) a += sq[r * Jp + j];
+            for (int q = lane; q < J4; q += 32) {
+                const float4 x = S4[q];
+                a += (x.x + x.y) + (x.z + x.w);
+            }
             a = warp_sum(a);
             if (lane == 0) d.mupart[(size_t)i * M + r] = a;
         }
+    }
+
+    // ---- log|det W_i| (FP64): pending scale and the sweep, log|1 - z_r| = -log(q_r)/2
+    if (tid == 0) {
+        double sp = 1.0;
+#pragma unroll
+        for (int r = 0; r < M; ++r) sp *= (double)scl[r];
+        d.logdet[i] += log(sp) - 0.5 * log(qprod);
     }
 }
 
 bool bin_phase_config(int M, int J, int* fpt, int* threads)
 {
+    // frames per thread 1, 2, 4 with at most 256 threads; 8 (M <= 4) with up to 512
     static const int cands[4] = {1, 2, 4, 8};
-    // prefer about 256 threads; fall back to 512 for the longest frames
-    for (int pass = 0; pass < 2; ++pass) {
-        const int cap = pass == 0 ? 256 : 512;
-        for (int c = 0; c < 4; ++c) {
-            const int f = cands[c];
-            if (M * f > 32) break;
-            const int nt = (J + f - 1) / f;
-            if (nt <= cap) {
-                *fpt = f;
-                *threads = ((nt + 31) / 32) * 32;
-                if (*threads < 64) *threads = 64;
-                return true;
-            }
+    for (int c = 0; c < 4; ++c) {
+        const int f = cands[c];
+        if (M * f > 32) break;
+        const int cap = f == 8 ? 512 : 256;
+        const int nt = (J + f - 1) / f;
+        if (nt <= cap) {
+            *fpt = f;
+            *threads = ((nt + 31) / 32) * 32;
+            if (*threads < 64) *threads = 64;
+            return true;
         }
     }
     return false;
@@ -261,13 +292,17 @@ size_t bin_phase_smem(const Shape& s)
     int fpt = 0, nt = 0;
     bin_phase_config(s.M, s.J, &fpt, &nt);
     const int NW = nt / 32;
-    return sizeof(float) * ((size_t)(s.M + 2 * s.N) * s.Jp + 2 * NW * 3 * s.M);
+    return sizeof(float) * ((size_t)s.N * (kLPad + s.Jp) + (size_t)(s.N + s.M) * s.Jp + 2 * NW * 3 * s.M);
 }
 
 template <int M, int FPT>
 static cudaError_t launch_mf(const Shape& s, const State& d, int v_tap0, int nt, cudaStream_t st,
                             bool configure_only)
 {
+    // 8 frames per thread: up to 512 threads, 128 registers; otherwise 256 threads and
+    // 4 CTAs per SM (64 registers) when the bin's samples take at most 24 registers
+    constexpr int kMaxT = FPT == 8 ? 512 : 256;
+    constexpr int kMinB = FPT == 8 ? 1 : (M * FPT >= 16 ? 2 : 4);
     if (configure_only) {
         // the device's opt-in maximum, so that handles of different J share the setting
         int dev = 0, optin = 0;
@@ -275,9 +310,12 @@ static cudaError_t launch_mf(const Shape& s, const State& d, int v_tap0, int nt,
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
         if ((size_t)optin < bin_phase_smem(s)) return cudaErrorInvalidValue;
-        return cudaFuncSetAttribute(bin_phase_kernel<M, FPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        return cudaFuncSetAttribute(bin_phase_kernel<M, FPT, kMaxT, kMinB>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     }
-    bin_phase_kernel<M, FPT><<<s.F, nt, bin_phase_smem(s), st>>>(s, d, v_tap0);
+    // float4 views of the staged rows need 16-byte aligned row starts
+    if (s.Jp % 8 != 0 || nt > kMaxT) return cudaErrorInvalidValue;
+    bin_phase_kernel<M, FPT, kMaxT, kMinB><<<s.F, nt, bin_phase_smem(s), st>>>(s, d, v_tap0);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ cudaError_t launch_init_nmf(const Shape& s, const State& d, const float* T0, con
 cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t configure_bin_phase(const Shape& s);
 cudaError_t launch_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
+cudaError_t configure_frame_phase();
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st);
 cudaError_t launch_finalize(const Shape& s, const State& d, cudaStream_t st);

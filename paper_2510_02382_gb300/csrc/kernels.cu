@@ -138,47 +138,67 @@ cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st)
 // Then the normalisation of Eqs. 19-21: mu_r = sqrt(sum_{i,j} |y_r|^2 / (F J)) from the
 // per-bin sums, and the PSD of the next iteration, 1/lambda with T'' = T' mu_{(n,0)}^{-2}.
 // The pending scale 1/mu_r (applied to Y, W, T by the next bin phase) is written by
-// CTA (0,0). Threads: tx = tid & 7 is the frame, ty = tid >> 3 the bin slice.
+// CTA (0,0). Threads: tx = tid & 7 is the frame, ty = tid >> 3 the bin slice. The bases
+// of source n and the tile's P are staged in shared memory, FC bins at a time.
+constexpr int kFrameTile = 8;
+constexpr int kFrameSmemBytes = 48 * 1024;
+
+// Bins staged per chunk: a multiple of 4 so that the P block after FC*B floats of bases
+// starts on a 16-byte boundary (it is written with float4 stores).
+__host__ __device__ inline int frame_chunk_bins(int B)
+{
+    return (kFrameSmemBytes / (4 * (B + kFrameTile))) & ~3;
+}
+
 template <int BB>
 __global__ void __launch_bounds__(256) frame_phase_kernel(const Shape s, const State d,
                                                           const int v_tap0, const int normalize)
 {
-    __shared__ float red[8][2 * BB][8];
-    __shared__ float vnew[BB][8];
-    __shared__ double dred[8][CTFMNMF_MAX_M];
+    extern __shared__ float4 fsm4[];
+    float* fsm = reinterpret_cast<float*>(fsm4);
+    __shared__ float red[8][2 * BB][kFrameTile];
+    __shared__ float vnew[BB][kFrameTile];
+    __shared__ float fred[8][CTFMNMF_MAX_M];
     __shared__ float s_scale[CTFMNMF_MAX_M];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tid & 7, ty = tid >> 3;
     const int n = blockIdx.y;
-    const int j = blockIdx.x * 8 + tx;
+    const int j0 = blockIdx.x * kFrameTile;
+    const int j = j0 + tx;
     const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
+    const int FC = frame_chunk_bins(B);
+    float* Ts = fsm;                     // [FC][B]  bases of source n
+    float* Ps = fsm + FC * B;            // [FC][8]  delayed power of the tile's frames
 
-    // ---- normalisation factors from the per-bin row powers (FP64 sum)
+    // ---- normalisation factors from the per-bin row powers (FP32 tree sums)
     {
-        double acc[CTFMNMF_MAX_M];
+        float acc[CTFMNMF_MAX_M];
 #pragma unroll
-        for (int r = 0; r < CTFMNMF_MAX_M; ++r) acc[r] = 0.0;
+        for (int r = 0; r < CTFMNMF_MAX_M; ++r) acc[r] = 0.f;
         for (int i = tid; i < F; i += 256) {
 #pragma unroll
             for (int r = 0; r < CTFMNMF_MAX_M; ++r)
-                if (r < M) acc[r] += (double)d.mupart[(size_t)i * M + r];
+                if (r < M) acc[r] += d.mupart[(size_t)i * M + r];
         }
 #pragma unroll
         for (int r = 0; r < CTFMNMF_MAX_M; ++r) {
             if (r >= M) break;
-            const double v = warp_sum_d(acc[r]);
-            if (lane == 0) dred[warp][r] = v;
+            const float v = warp_sum(acc[r]);
+            if (lane == 0) fred[warp][r] = v;
         }
         __syncthreads();
         if (tid < M) {
-            double t = 0.0;
-            for (int w = 0; w < 8; ++w) t += dred[w][tid];
-            const double mu = sqrt(t / ((double)F * (double)J));
-            const float sc = (normalize && mu > 0.0) ? (float)(1.0 / mu) : 1.0f;
+            float t = 0.f;
+            for (int w = 0; w < 8; ++w) t += fred[w][tid];
+            const float ms = t / ((float)F * (float)J);
+            float sc = 1.0f;
+            if (normalize && ms > 0.f) {
+                const float r0 = rsqrtf(ms);
+                sc = r0 * fmaf(-0.5f * ms * r0, r0, 1.5f);
+            }
             s_scale[tid] = sc;
             if (blockIdx.x == 0 && blockIdx.y == 0) d.scale[tid] = sc;
         }
-        __syncthreads();
     }
 
     const bool valid = j < J;
@@ -191,23 +211,36 @@ __global__ void __launch_bounds__(256) frame_phase_kernel(const Shape s, const S
     float an[BB], ad[BB];
 #pragma unroll
     for (int k = 0; k < BB; ++k) { an[k] = 0.f; ad[k] = 0.f; }
-    if (valid) {
-        for (int i = ty; i < F; i += 32) {
-            const float* Ti = d.T + ((size_t)i * N + n) * B;
-            float t[BB];
-            float lam = 0.f;
+    for (int c0 = 0; c0 < F; c0 += FC) {
+        const int nb = min(FC, F - c0);
+        __syncthreads();
+        for (int e = tid; e < nb * B; e += 256) {
+            const int ii = e / B, k = e - ii * B;
+            Ts[e] = d.T[((size_t)(c0 + ii) * N + n) * B + k];
+        }
+        for (int e = tid; e < nb * 2; e += 256) {
+            const int ii = e >> 1, h = e & 1;
+            reinterpret_cast<float4*>(Ps)[e] =
+                reinterpret_cast<const float4*>(d.P + ((size_t)(c0 + ii) * N + n) * Jp + j0)[h];
+        }
+        __syncthreads();
+        if (valid) {
+            for (int ii = ty; ii < nb; ii += 32) {
+                float t[BB];
+                float lam = 0.f;
 #pragma unroll
-            for (int k = 0; k < BB; ++k) {
-                t[k] = k < B ? Ti[k] : 0.f;
-                lam = fmaf(t[k], vk[k], lam);
-            }
-            const float il = 1.0f / fmaxf(lam, kFloorPsd);
-            const float g = d.P[((size_t)i * N + n) * Jp + j] * il * il;
-            const float h = cnt * il;
+                for (int k = 0; k < BB; ++k) {
+                    t[k] = k < B ? Ts[ii * B + k] : 0.f;
+                    lam = fmaf(t[k], vk[k], lam);
+                }
+                const float il = 1.0f / fmaxf(lam, kFloorPsd);
+                const float g = Ps[ii * kFrameTile + tx] * il * il;
+                const float h = cnt * il;
 #pragma unroll
-            for (int k = 0; k < BB; ++k) {
-                an[k] = fmaf(t[k], g, an[k]);
-                ad[k] = fmaf(t[k], h, ad[k]);
+                for (int k = 0; k < BB; ++k) {
+                    an[k] = fmaf(t[k], g, an[k]);
+                    ad[k] = fmaf(t[k], h, ad[k]);
+                }
             }
         }
     }
@@ -225,9 +258,9 @@ __global__ void __launch_bounds__(256) frame_phase_kernel(const Shape s, const S
         }
     }
     __syncthreads();
-    for (int t = tid; t < B * 8; t += 256) {
+    for (int t = tid; t < B * kFrameTile; t += 256) {
         const int k = t >> 3, x = t & 7;
-        const int jj = blockIdx.x * 8 + x;
+        const int jj = j0 + x;
         float num = 0.f, den = 0.f;
 #pragma unroll
         for (int w = 0; w < 8; ++w) { num += red[w][k][x]; den += red[w][BB + k][x]; }
@@ -247,23 +280,57 @@ __global__ void __launch_bounds__(256) frame_phase_kernel(const Shape s, const S
     const float t2 = s0 * s0;
 #pragma unroll
     for (int k = 0; k < BB; ++k) vk[k] = k < B ? vnew[k][tx] : 0.f;
-    for (int i = ty; i < F; i += 32) {
-        const float* Ti = d.T + ((size_t)i * N + n) * B;
-        float lam = 0.f;
+    for (int c0 = 0; c0 < F; c0 += FC) {
+        const int nb = min(FC, F - c0);
+        if (c0 > 0) {                       // the first chunk is still staged when F <= FC
+            __syncthreads();
+            for (int e = tid; e < nb * B; e += 256) {
+                const int ii = e / B, k = e - ii * B;
+                Ts[e] = d.T[((size_t)(c0 + ii) * N + n) * B + k];
+            }
+            __syncthreads();
+        } else if (F > FC) {
+            __syncthreads();
+            for (int e = tid; e < nb * B; e += 256) {
+                const int ii = e / B, k = e - ii * B;
+                Ts[e] = d.T[((size_t)ii * N + n) * B + k];
+            }
+            __syncthreads();
+        }
+        for (int ii = ty; ii < nb; ii += 32) {
+            float lam = 0.f;
 #pragma unroll
-        for (int k = 0; k < BB; ++k) lam = fmaf(k < B ? Ti[k] : 0.f, vk[k], lam);
-        d.invlam[((size_t)i * N + n) * Jp + j] = valid ? 1.0f / fmaxf(lam * t2, kFloorPsd) : 0.f;
+            for (int k = 0; k < BB; ++k) lam = fmaf(k < B ? Ts[ii * B + k] : 0.f, vk[k], lam);
+            d.invlam[((size_t)(c0 + ii) * N + n) * Jp + j] = valid ? 1.0f / fmaxf(lam * t2, kFloorPsd) : 0.f;
+        }
     }
+}
+
+// Allow the frame-phase kernels more than 48 KB of shared memory (dynamic + static).
+cudaError_t configure_frame_phase()
+{
+    const int bytes = kFrameSmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(frame_phase_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(frame_phase_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(frame_phase_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(frame_phase_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st)
 {
-    const dim3 grid(s.Jp / 8, s.N);
-    if (s.B <= 4) frame_phase_kernel<4><<<grid, 256, 0, st>>>(s, d, v_tap0, normalize);
-    else if (s.B <= 8) frame_phase_kernel<8><<<grid, 256, 0, st>>>(s, d, v_tap0, normalize);
-    else if (s.B <= 16) frame_phase_kernel<16><<<grid, 256, 0, st>>>(s, d, v_tap0, normalize);
-    else frame_phase_kernel<32><<<grid, 256, 0, st>>>(s, d, v_tap0, normalize);
+    const dim3 grid(s.Jp / kFrameTile, s.N);
+    const int FC = frame_chunk_bins(s.B);
+    if (FC < 4 || (FC * s.B) % 4 != 0 || s.Jp % kFrameTile != 0) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * (size_t)FC * (s.B + kFrameTile);
+    if (s.B <= 4) frame_phase_kernel<4><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
+    else if (s.B <= 8) frame_phase_kernel<8><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
+    else if (s.B <= 16) frame_phase_kernel<16><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
+    else frame_phase_kernel<32><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,8 @@ def _create(lib, M, N, L, Bk, F, J):
     ((3, 2, 2, 4, 8, 2), -1),        # J <= longest tap count
     ((3, 2, 2, 4, -5, 16), -1),      # F <= 0
     ((4, 2, 2, 4, 8, 5000), -7),     # J too long for one block at M = 4
-    ((8, 2, 4, 4, 8, 3000), -7),     # J too long at M = 8
+    ((8, 2, 4, 4, 8, 1030), -7),     # J too long at M = 8
+    ((5, 2, 3, 4, 8, 1025), -7),     # J too long at M = 5
 ])
 def test_create_rejects_bad_shapes_on_host(lib, dims, code):
     rc, h = _create(lib, *dims)
@@ -85,9 +86,9 @@ def test_null_handle_calls_fail_cleanly(lib):
 
 
 def test_bin_phase_limits_match_header():
-    # J <= 4096 for M <= 4 and J <= 2048 for M = 5..8 (documented in ctfmnmf_create)
+    # J <= 4096 for M <= 4 and J <= 1024 for M = 5..8 (documented in ctfmnmf_create)
     text = open(HEADER).read()
-    assert "4096 (M <= 4)" in text and "2048 (M = 5..8)" in text
+    assert "4096 (M <= 4)" in text and "1024 (M = 5..8)" in text
 
 
 def test_default_factor_generator_reference_values():
