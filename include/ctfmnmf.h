@@ -67,10 +67,26 @@ typedef struct ctfmnmf_options {
     int v_update;              /* CTFMNMF_V_ALL_TAPS (default) or CTFMNMF_V_TAP0        */
     int normalize;             /* 1 (default): scale normalisation of Eqs. 19-21 after
                                   every iteration; 0: none                              */
-    int use_graph;             /* 1 (default): ctfmnmf_iterate replays a CUDA graph of
-                                  its launches; 0: plain stream launches                */
-    int reserved[5];           /* must be zero                                          */
+    int use_graph;             /* 1 (default): the two-kernel path replays a CUDA graph
+                                  of its launches; 0: plain stream launches             */
+    int path;                  /* CTFMNMF_PATH_AUTO (default), _TWO_KERNEL or _PERSISTENT */
+    int wait_timeout_ms;       /* bound of every device-side wait of the persistent path;
+                                  0 (default) = 2000 ms. A wait that runs out ends the
+                                  launch and the next ctfmnmf_synchronize (or any call that
+                                  synchronises) returns CTFMNMF_ETIMEOUT                 */
+    int reserved[3];           /* must be zero                                          */
 } ctfmnmf_options;
+
+/* Execution paths of ctfmnmf_iterate. PERSISTENT: all iterations of a call in one
+ * cooperative launch with a grid-wide barrier between the per-bin and the cross-bin
+ * steps (needs B <= 16, J <= 4096 for M <= 4 or J <= 2048 for M = 5..8, and enough
+ * co-resident thread blocks). TWO_KERNEL: one launch per step, replayed as a CUDA graph.
+ * AUTO: persistent when the shape allows it, else two-kernel. */
+enum {
+    CTFMNMF_PATH_AUTO = 0,
+    CTFMNMF_PATH_TWO_KERNEL = 1,
+    CTFMNMF_PATH_PERSISTENT = 2
+};
 
 typedef struct ctfmnmf* ctfmnmf_t;
 
@@ -84,7 +100,8 @@ void ctfmnmf_default_options(ctfmnmf_options* opt);
  * (the square model of Sec. II; M=4,6,8 with N=2 gives the paper's Table I).
  * EINVAL if a dimension is <= 0, N > M, M > CTFMNMF_MAX_M, B > CTFMNMF_MAX_B,
  * a derived L_n exceeds L, J <= max L_n, or out is NULL.
- * EUNSUPPORTED if J exceeds 4096 (M <= 4) or 1024 (M = 5..8).
+ * EUNSUPPORTED if J exceeds 4096 (M <= 4) or 1024 (M = 5..8), or if the options ask for
+ * the persistent path and the shape or the device does not allow it.
  * On success *out receives the handle; on failure *out is set to NULL.
  */
 int ctfmnmf_create(int M, int N, int L, int B, int F, int J, ctfmnmf_t* out);
@@ -140,6 +157,13 @@ int ctfmnmf_set_init(ctfmnmf_t h, const float* T0, const float* V0);
 int ctfmnmf_iterate(ctfmnmf_t h, int n_iter);
 
 /*
+ * Wait for all work enqueued on the handle's stream and report device-side failures:
+ * CTFMNMF_ETIMEOUT if a bounded device wait ran out since the last report (the solver
+ * state is then undefined until the next ctfmnmf_load_stft), CTFMNMF_ECUDA on a CUDA error.
+ */
+int ctfmnmf_synchronize(ctfmnmf_t h);
+
+/*
  * Negative log-likelihood of Eq. 5 without its constant, at the current state:
  * sum over bins, rows r=(n,l) and frames j >= l of log lambda_{n,i,j-l} +
  * |y_{r,i,j}|^2 / lambda_{n,i,j-l}, minus 2 J sum_i log|det W_i|.
@@ -185,6 +209,26 @@ int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms);
 /* Number of kernels this handle has enqueued since it was created (host counter; a graph
  * replay counts every kernel node in it). Writes one int64 to *count (host). */
 int ctfmnmf_get_launch_count(ctfmnmf_t h, long long* count);
+
+/* Which path ctfmnmf_iterate takes for this handle: CTFMNMF_PATH_TWO_KERNEL or
+ * CTFMNMF_PATH_PERSISTENT, written to *path (host). */
+int ctfmnmf_get_path(ctfmnmf_t h, int* path);
+
+/*
+ * Persistent path only: run one launch of n_iter >= 1 iterations with a CUDA event pair
+ * around the persistent kernel and another around the closing normalisation kernels;
+ * synchronise; write the two durations in milliseconds to ms[2] (host). The state
+ * advances by n_iter iterations. EUNSUPPORTED if the handle uses the two-kernel path.
+ */
+int ctfmnmf_time_persistent(ctfmnmf_t h, int n_iter, double* ms);
+
+/*
+ * Test hook for the bounded device waits: at the next persistent launch, thread block
+ * `cta` does not arrive at the first grid barrier, so every other block's wait runs out
+ * after wait_timeout_ms and the launch ends; ctfmnmf_synchronize then returns
+ * CTFMNMF_ETIMEOUT and the state must be reloaded (ctfmnmf_load_stft). cta < 0 clears it.
+ */
+int ctfmnmf_debug_skip_arrival(ctfmnmf_t h, int cta);
 
 #ifdef __cplusplus
 }

@@ -25,8 +25,11 @@ class Dims(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("v_update", c_int), ("normalize", c_int), ("use_graph", c_int),
-                ("reserved", c_int * 5)]
+    _fields_ = [("v_update", c_int), ("normalize", c_int), ("use_graph", c_int), ("path", c_int),
+                ("wait_timeout_ms", c_int), ("reserved", c_int * 3)]
+
+
+PATHS = {"auto": 0, "two_kernel": 1, "persistent": 2}
 
 
 class CtfMnmfError(RuntimeError):
@@ -59,6 +62,10 @@ _SIGS = {
     "ctfmnmf_get_nmf": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ctfmnmf_time_phases": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_get_launch_count": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_synchronize": (c_int, [c_void_p]),
+    "ctfmnmf_get_path": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_time_persistent": (c_int, [c_void_p, c_int, c_void_p]),
+    "ctfmnmf_debug_skip_arrival": (c_int, [c_void_p, c_int]),
 }
 
 
@@ -103,7 +110,8 @@ class CTFMNMF:
 
     def __init__(self, M: int, N: int, L: int, B: int, F: int, J: int,
                  Ln: Optional[Sequence[int]] = None, v_update: str = "all_taps",
-                 normalize: bool = True, use_graph: bool = True, stream=None):
+                 normalize: bool = True, use_graph: bool = True, path: str = "auto",
+                 wait_timeout_ms: int = 0, stream=None):
         import torch
         self.M, self.N, self.L, self.B, self.F, self.J = M, N, L, B, F, J
         d = Dims(M, N, L, B, F, J)
@@ -112,6 +120,8 @@ class CTFMNMF:
         o.v_update = {"all_taps": V_ALL_TAPS, "tap0": V_TAP0}[v_update]
         o.normalize = int(bool(normalize))
         o.use_graph = int(bool(use_graph))
+        o.path = PATHS[path]
+        o.wait_timeout_ms = int(wait_timeout_ms)
         ln_arr = (c_int * N)(*Ln) if Ln is not None else None
         h = c_void_p()
         rc = lib().ctfmnmf_create_ex(ctypes.byref(d), ln_arr, ctypes.byref(o), ctypes.byref(h))
@@ -122,6 +132,9 @@ class CTFMNMF:
         taps = (c_int * N)()
         _check(lib().ctfmnmf_get_taps(self._h, taps), self._h)
         self.Ln = list(taps)
+        p = c_int()
+        _check(lib().ctfmnmf_get_path(self._h, ctypes.byref(p)), self._h)
+        self.path = {1: "two_kernel", 2: "persistent"}[p.value]
 
     # -- lifecycle
     def close(self):
@@ -210,6 +223,18 @@ class CTFMNMF:
         ms = (c_double * 2)()
         _check(lib().ctfmnmf_time_phases(self._h, int(n_iter), ms), self._h)
         return float(ms[0]), float(ms[1])
+
+    def synchronize(self):
+        _check(lib().ctfmnmf_synchronize(self._h), self._h)
+
+    def time_persistent(self, n_iter: int):
+        """Device ms of one persistent launch of n_iter iterations, and of the closing kernels."""
+        ms = (c_double * 2)()
+        _check(lib().ctfmnmf_time_persistent(self._h, int(n_iter), ms), self._h)
+        return float(ms[0]), float(ms[1])
+
+    def debug_skip_arrival(self, cta: int):
+        _check(lib().ctfmnmf_debug_skip_arrival(self._h, int(cta)), self._h)
 
     def launch_count(self) -> int:
         out = ctypes.c_longlong()

@@ -26,6 +26,10 @@ struct ctfmnmf {
     double* host_cost;          // pinned one-double landing buffer
     float2* sepbuf;             // device images for ctfmnmf_get_separated_host (lazy)
     long long launches;         // kernels enqueued so far
+    ctf::PersistPlan plan;      // persistent-path plan for this shape on this device
+    int path;                   // CTFMNMF_PATH_TWO_KERNEL or CTFMNMF_PATH_PERSISTENT
+    int skip_cta;               // test hook: block that skips its first barrier arrival
+    unsigned long long timeout_ns;
     char err[256];
 };
 
@@ -53,7 +57,7 @@ void free_state(ctfmnmf* h)
 {
     State& d = h->d;
     void* ptrs[] = {d.Y, d.W, d.logdet, d.T, d.V, d.invlam, d.P, d.mupart, d.scale, d.flag,
-                    d.cost_part, d.cost_out, d.staging};
+                    d.cost_part, d.cost_out, d.staging, d.ldm, d.lde, d.sync};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     memset(&h->d, 0, sizeof(h->d));
@@ -82,6 +86,21 @@ int check_flag(ctfmnmf* h, int mask, const char* what)
 // kernels per launcher: load 1, init_nmf 1, psd 1, bin/frame phase 1 each, finalize 2,
 // cost 2, separate 1, read-outs 1
 constexpr int kFinalizeKernels = 2;
+
+// Synchronise the stream and report a device wait that ran out (then clear the report).
+int sync_and_check(ctfmnmf* h)
+{
+    int flag = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&flag, h->d.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (flag) {
+        CUDA_TRY(h, cudaMemsetAsync(h->d.flag + 1, 0, sizeof(int), h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        h->loaded = false;
+        return fail(h, CTFMNMF_ETIMEOUT, "a device-side wait of the persistent kernel ran out");
+    }
+    return CTFMNMF_OK;
+}
 
 int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
 {
@@ -136,13 +155,17 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
             return fail(nullptr, CTFMNMF_EINVAL, "unknown v_update %d", o.v_update);
         if ((o.normalize != 0 && o.normalize != 1) || (o.use_graph != 0 && o.use_graph != 1))
             return fail(nullptr, CTFMNMF_EINVAL, "normalize and use_graph must be 0 or 1");
-        for (int k = 0; k < 5; ++k)
+        if (o.path < CTFMNMF_PATH_AUTO || o.path > CTFMNMF_PATH_PERSISTENT)
+            return fail(nullptr, CTFMNMF_EINVAL, "unknown path %d", o.path);
+        if (o.wait_timeout_ms < 0) return fail(nullptr, CTFMNMF_EINVAL, "wait_timeout_ms must be >= 0");
+        for (int k = 0; k < 3; ++k)
             if (o.reserved[k]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
     }
     Shape s;
     memset(&s, 0, sizeof(s));
     s.M = M; s.N = N; s.B = B; s.F = F; s.J = J;
     s.Jp = (J + 7) / 8 * 8;
+    s.FBp = (F * B + 3) / 4 * 4;
     int total = 0, lmax = 0;
     for (int n = 0; n < N; ++n) {
         const int t = Ln ? Ln[n] : M / N + (n < M % N ? 1 : 0);
@@ -177,7 +200,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         {(void**)&d.Y, sizeof(float2) * MF * s.Jp},
         {(void**)&d.W, sizeof(float2) * MF * M},
         {(void**)&d.logdet, sizeof(double) * F},
-        {(void**)&d.T, sizeof(float) * (size_t)F * N * B},
+        {(void**)&d.T, sizeof(float) * (size_t)N * s.FBp},
         {(void**)&d.V, sizeof(float) * (size_t)N * B * s.Jp},
         {(void**)&d.invlam, sizeof(float) * FNJ},
         {(void**)&d.P, sizeof(float) * FNJ},
@@ -186,6 +209,9 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         {(void**)&d.flag, sizeof(int) * 4},
         {(void**)&d.cost_part, sizeof(double) * F},
         {(void**)&d.cost_out, sizeof(double)},
+        {(void**)&d.ldm, sizeof(double) * F},
+        {(void**)&d.lde, sizeof(int) * F},
+        {(void**)&d.sync, sizeof(unsigned) * (32 + ctf::kMaxPersistCtas)},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -201,6 +227,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         rc = CTFMNMF_ECUDA;
     }
     if (rc == CTFMNMF_OK && (cudaMemset(d.flag, 0, sizeof(int) * 4) != cudaSuccess ||
+                             cudaMemset(d.sync, 0, sizeof(unsigned) * (32 + ctf::kMaxPersistCtas)) != cudaSuccess ||
                              cudaMemset(d.P, 0, sizeof(float) * FNJ) != cudaSuccess ||
                              cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
         rc = CTFMNMF_ECUDA;
@@ -216,6 +243,17 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         delete h;
         return fail(nullptr, rc, "device set-up failed: %s", msg);
     }
+    h->skip_cta = -1;
+    h->timeout_ns = 1000000ull * (unsigned long long)(o.wait_timeout_ms > 0 ? o.wait_timeout_ms : 2000);
+    h->plan = ctf::plan_persistent(s);
+    cudaGetLastError();
+    if (o.path == CTFMNMF_PATH_PERSISTENT && !h->plan.ok) {
+        free_state(h);
+        delete h;
+        return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the persistent path does not fit this shape on this device");
+    }
+    h->path = (o.path != CTFMNMF_PATH_TWO_KERNEL && h->plan.ok) ? CTFMNMF_PATH_PERSISTENT
+                                                                 : CTFMNMF_PATH_TWO_KERNEL;
     *out = h;
     return CTFMNMF_OK;
 }
@@ -252,6 +290,7 @@ int ctfmnmf_load_stft(ctfmnmf_t h, const void* X)
     if (!X) return fail(h, CTFMNMF_EINVAL, "X is NULL");
     h->err[0] = 0;
     h->loaded = false;
+    CUDA_TRY(h, cudaMemsetAsync(h->d.flag + 1, 0, sizeof(int), h->stream));
     CUDA_TRY(h, ctf::launch_load(h->s, h->d, (const float2*)X, h->stream));
     CUDA_TRY(h, ctf::launch_psd(h->s, h->d, h->stream));
     h->launches += 2;
@@ -294,6 +333,15 @@ int ctfmnmf_iterate(ctfmnmf_t h, int n_iter)
     if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
     h->err[0] = 0;
     if (n_iter == 0) return CTFMNMF_OK;
+    if (h->path == CTFMNMF_PATH_PERSISTENT) {
+        const int tap0 = h->opt.v_update == CTFMNMF_V_TAP0;
+        CUDA_TRY(h, ctf::launch_persistent(h->s, h->d, h->plan, n_iter, tap0, h->opt.normalize, h->timeout_ns,
+                                           h->skip_cta, h->stream));
+        h->skip_cta = -1;
+        CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, h->stream));
+        h->launches += 1 + kFinalizeKernels;
+        return CTFMNMF_OK;
+    }
     if (!h->opt.use_graph) {
         const int rc = enqueue_iterations(h, n_iter, h->stream);
         if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter);
@@ -331,6 +379,10 @@ int ctfmnmf_cost(ctfmnmf_t h, double* out)
     if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
     if (!out) return fail(h, CTFMNMF_EINVAL, "out is NULL");
     if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    {
+        const int rc = sync_and_check(h);
+        if (rc != CTFMNMF_OK) return rc;
+    }
     CUDA_TRY(h, ctf::launch_cost(h->s, h->d, h->stream));
     h->launches += 2;
     CUDA_TRY(h, cudaMemcpyAsync(h->host_cost, h->d.cost_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -364,6 +416,10 @@ int ctfmnmf_get_separated_host(ctfmnmf_t h, void* C)
     CUDA_TRY(h, ctf::launch_separate(h->s, h->d, h->sepbuf, h->stream));
     h->launches += 1;
     CUDA_TRY(h, cudaMemcpyAsync(C, h->sepbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
+    {
+        const int rc = sync_and_check(h);
+        if (rc != CTFMNMF_OK) return rc;
+    }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CTFMNMF_OK;
 }
@@ -437,6 +493,60 @@ int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms)
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     ms[0] = tot[0] / n_iter;
     ms[1] = tot[1] / n_iter;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_synchronize(ctfmnmf_t h)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    return sync_and_check(h);
+}
+
+int ctfmnmf_get_path(ctfmnmf_t h, int* path)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!path) return fail(h, CTFMNMF_EINVAL, "path is NULL");
+    *path = h->path;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_time_persistent(ctfmnmf_t h, int n_iter, double* ms)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!ms || n_iter < 1) return fail(h, CTFMNMF_EINVAL, "need n_iter >= 1 and an output");
+    if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");
+    if (h->path != CTFMNMF_PATH_PERSISTENT) return fail(h, CTFMNMF_EUNSUPPORTED, "handle uses the two-kernel path");
+    const int tap0 = h->opt.v_update == CTFMNMF_V_TAP0;
+    cudaEvent_t ev[4];
+    for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+    cudaError_t e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess)
+        e = ctf::launch_persistent(h->s, h->d, h->plan, n_iter, tap0, h->opt.normalize, h->timeout_ns, -1,
+                                   h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess) e = ctf::launch_finalize(h->s, h->d, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2], ev[3]);
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(h, CTFMNMF_ECUDA, "persistent timing: %s", cudaGetErrorString(e));
+    h->launches += 1 + kFinalizeKernels;
+    const int rc = sync_and_check(h);
+    if (rc != CTFMNMF_OK) return rc;
+    ms[0] = a;
+    ms[1] = b;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_debug_skip_arrival(ctfmnmf_t h, int cta)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (cta >= 0 && h->path != CTFMNMF_PATH_PERSISTENT)
+        return fail(h, CTFMNMF_EUNSUPPORTED, "handle uses the two-kernel path");
+    h->skip_cta = cta < 0 ? -1 : cta;
     return CTFMNMF_OK;
 }
 

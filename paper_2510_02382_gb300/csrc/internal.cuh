@@ -5,26 +5,31 @@
 //                                 contiguous block of M*Jp*8 bytes (Jp = J rounded up to 4)
 //   W      [F][M][M]   complex64  row r of W_i holds w_r^H
 //   logdet [F]         float64    log|det W_i|, tracked by the determinant lemma
-//   T      [F][N][B]   float32    bases, bin-major (the API shape is [N][F][B])
+//   T      [N][FBp]    float32    bases, T[n][i][k] at n*FBp + i*B + k (the API shape [N][F][B]
+//                                 with each source block padded to 16 bytes)
 //   V      [N][B][Jp]  float32    activations (padding frames are 0)
 //   invlam [F][N][Jp]  float32    1/lambda_{n,i,j} for the current T, V (padding 0)
 //   P      [F][N][Jp]  float32    delayed row power feeding the activation update
 //   mupart [F][M]      float32    per-bin row power sums feeding the normalisation
 //   scale  [M]         float32    pending normalisation 1/mu_r not yet applied to Y, W, T
+//   ldm, lde [F]       f64, i32   running product of |det| factors (mantissa, exponent),
+//                                 folded into logdet at the end of every iterate call
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/ctfmnmf.h"
+#include "ctfmnmf.h"
 
 namespace ctf {
 
+constexpr int kMaxPersistCtas = 1024; // grid barrier flags reserved per handle
 constexpr float kFloorNmf = 1e-12f;   // floor of T and V after each multiplicative update
 constexpr float kFloorPsd = 1e-18f;   // floor of lambda where it is formed
 
 struct Shape {
     int M, N, B, F, J, Jp;
+    int FBp;                    // per-source stride of T: F*B rounded up to a multiple of 4
     int Ln[CTFMNMF_MAX_M];
     int row_n[CTFMNMF_MAX_M];   // extended row r -> source n
     int row_l[CTFMNMF_MAX_M];   // extended row r -> tap l
@@ -41,7 +46,10 @@ struct State {
     float* P;
     float* mupart;
     float* scale;
-    int* flag;          // [0]: non-finite input seen
+    double* ldm;        // [F] mantissa of the log-det product not yet folded into logdet
+    int* lde;           // [F] its binary exponent
+    unsigned* sync;     // [32 + kMaxPersistCtas] grid barrier: [0] abort word, [32 + b] flag of CTA b
+    int* flag;          // [0]: non-finite input seen, [1]: device wait timed out
     double* cost_part;  // [F] per-bin cost
     double* cost_out;   // [1]
     float2* staging;    // host-loaded STFT staging [M][F][J]
@@ -64,6 +72,23 @@ cudaError_t launch_separate(const Shape& s, const State& d, float2* out, cudaStr
 cudaError_t launch_get_demixed(const Shape& s, const State& d, float2* out, cudaStream_t st);
 cudaError_t launch_get_nmf(const Shape& s, const State& d, float* T, float* V, cudaStream_t st);
 
+// Persistent path: all iterations in one cooperative launch (persistent.cu).
+struct PersistPlan {
+    int ok;          // shape supported by the persistent kernel
+    int fpt, gt;     // frames per thread, threads per group
+    int groups;      // groups per CTA
+    int gsm;         // shared floats per group
+    int res_floats;  // shared floats per group for the resident rows and W_i (0: streaming)
+    int fc;          // bins per frame-phase chunk
+    int resident;    // 1: Y and W stay in shared memory across iterations
+    int ctas;        // CTAs launched
+    size_t smem;     // dynamic shared bytes per CTA
+};
+PersistPlan plan_persistent(const Shape& s);
+cudaError_t launch_persistent(const Shape& s, const State& d, const PersistPlan& p, int n_iter,
+                              int v_tap0, int normalize, unsigned long long timeout_ns, int skip_cta,
+                              cudaStream_t st);
+
 // Frames per thread / threads per block chosen for the bin phase; false if unsupported.
 bool bin_phase_config(int M, int J, int* fpt, int* threads);
 size_t bin_phase_smem(const Shape& s);
@@ -74,6 +99,24 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {   // a * conj(
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// 1/x for normal positive x: the hardware reciprocal estimate refined by one Newton-Raphson
+// step r <- r (2 - x r), which squares its relative error (about 1 ulp after the step).
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * fmaf(-x, r, 2.0f);
+}
+
+// Asynchronous global -> shared copies (cp.async): every thread issues its copies, then
+// cp_async_wait() and a barrier make them visible. The 16-byte form reads through L2 only.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -3,7 +3,7 @@
 // source images and the read-outs.
 #include <math.h>
 
-#include "internal.cuh"
+#include "phases.cuh"
 
 namespace ctf {
 
@@ -27,7 +27,11 @@ __global__ void load_kernel(const Shape s, const State d, const float2* __restri
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(d.flag, 1);
     if (threadIdx.x < M) d.W[((size_t)i * M + m) * M + threadIdx.x] = make_float2(m == (int)threadIdx.x ? 1.f : 0.f, 0.f);
-    if (m == 0 && threadIdx.x == 0) d.logdet[i] = 0.0;
+    if (m == 0 && threadIdx.x == 0) {
+        d.logdet[i] = 0.0;
+        d.ldm[i] = 1.0;
+        d.lde[i] = 0;
+    }
     if (i == 0 && m == 0 && threadIdx.x < M) d.scale[threadIdx.x] = 1.f;
 }
 
@@ -73,7 +77,7 @@ __global__ void init_nmf_kernel(const Shape s, const State d, const float* __res
             else if (use_default) v = default_factor(seed, 2 * e);
             else continue;
             bad |= !isfinite(v);
-            d.T[((size_t)i * N + n) * B + k] = fmaxf(v, kFloorNmf);
+            d.T[(size_t)n * s.FBp + (size_t)i * B + k] = fmaxf(v, kFloorNmf);
         } else {
             const size_t f = e - nT;               // index into V [N][B][Jp]
             const int j = (int)(f % Jp);
@@ -112,12 +116,13 @@ __global__ void psd_kernel(const Shape s, const State d)
         const int j = (int)(e % Jp);
         const size_t in = e / Jp;
         const int n = (int)(in % N);
+        const int i = (int)(in / N);
         float out = 0.f;
         if (j < J) {
-            const float* Ti = d.T + in * B;
+            const float* Ti = d.T + (size_t)n * s.FBp + (size_t)i * B;
             float lam = 0.f;
             for (int k = 0; k < B; ++k) lam = fmaf(Ti[k], d.V[((size_t)n * B + k) * Jp + j], lam);
-            out = 1.0f / fmaxf(lam, kFloorPsd);
+            out = recip(fmaxf(lam, kFloorPsd));
         }
         d.invlam[e] = out;
     }
@@ -130,181 +135,36 @@ cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st)
 }
 
 // ------------------------------------------------------------------ frame phase
-// One CTA per (8-frame tile, source n). Per frame j of the tile (Eq. 18, all-taps form
-// by default):
-//   lambda'_{n,i,j} = sum_k T'[i][n][k] V[n][k][j]  with T' the bases just updated,
-//   num[k] = sum_i T'[i][n][k] P[i][n][j] / lambda'^2,  den[k] = sum_i T'[i][n][k] c_n(j) / lambda',
-//   V[n][k][j] <- max(V sqrt(num/den), floor).
-// Then the normalisation of Eqs. 19-21: mu_r = sqrt(sum_{i,j} |y_r|^2 / (F J)) from the
-// per-bin sums, and the PSD of the next iteration, 1/lambda with T'' = T' mu_{(n,0)}^{-2}.
-// The pending scale 1/mu_r (applied to Y, W, T by the next bin phase) is written by
-// CTA (0,0). Threads: tx = tid & 7 is the frame, ty = tid >> 3 the bin slice. The bases
-// of source n and the tile's P are staged in shared memory, FC bins at a time.
-constexpr int kFrameTile = 8;
+// Two-kernel path: one CTA (one group of 256 threads) per (8-frame tile, source) item; the
+// device code is frame_item() in phases.cuh. The CTA first forms the normalisation scale
+// from the per-bin row powers; CTA 0 stores it as the pending scale of the next bin phase.
+constexpr int kFrameThreads = 256;
 constexpr int kFrameSmemBytes = 48 * 1024;
 
-// Bins staged per chunk: a multiple of 4 so that the P block after FC*B floats of bases
-// starts on a 16-byte boundary (it is written with float4 stores).
-__host__ __device__ inline int frame_chunk_bins(int B)
-{
-    return (kFrameSmemBytes / (4 * (B + kFrameTile))) & ~3;
-}
-
 template <int BB>
-__global__ void __launch_bounds__(256) frame_phase_kernel(const Shape s, const State d,
-                                                          const int v_tap0, const int normalize)
+__global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape s, const State d,
+                                                                    const int v_tap0, const int normalize,
+                                                                    const int FC)
 {
     extern __shared__ float4 fsm4[];
-    float* fsm = reinterpret_cast<float*>(fsm4);
-    __shared__ float red[8][2 * BB][kFrameTile];
-    __shared__ float vnew[BB][kFrameTile];
-    __shared__ float fred[8][CTFMNMF_MAX_M];
     __shared__ float s_scale[CTFMNMF_MAX_M];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tid & 7, ty = tid >> 3;
-    const int n = blockIdx.y;
-    const int j0 = blockIdx.x * kFrameTile;
-    const int j = j0 + tx;
-    const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
-    const int FC = frame_chunk_bins(B);
-    float* Ts = fsm;                     // [FC][B]  bases of source n
-    float* Ps = fsm + FC * B;            // [FC][8]  delayed power of the tile's frames
-
-    // ---- normalisation factors from the per-bin row powers (FP32 tree sums)
-    {
-        float acc[CTFMNMF_MAX_M];
-#pragma unroll
-        for (int r = 0; r < CTFMNMF_MAX_M; ++r) acc[r] = 0.f;
-        for (int i = tid; i < F; i += 256) {
-#pragma unroll
-            for (int r = 0; r < CTFMNMF_MAX_M; ++r)
-                if (r < M) acc[r] += d.mupart[(size_t)i * M + r];
-        }
-#pragma unroll
-        for (int r = 0; r < CTFMNMF_MAX_M; ++r) {
-            if (r >= M) break;
-            const float v = warp_sum(acc[r]);
-            if (lane == 0) fred[warp][r] = v;
-        }
-        __syncthreads();
-        if (tid < M) {
-            float t = 0.f;
-            for (int w = 0; w < 8; ++w) t += fred[w][tid];
-            const float ms = t / ((float)F * (float)J);
-            float sc = 1.0f;
-            if (normalize && ms > 0.f) {
-                const float r0 = rsqrtf(ms);
-                sc = r0 * fmaf(-0.5f * ms * r0, r0, 1.5f);
-            }
-            s_scale[tid] = sc;
-            if (blockIdx.x == 0 && blockIdx.y == 0) d.scale[tid] = sc;
-        }
-    }
-
-    const bool valid = j < J;
-    float vk[BB];
-#pragma unroll
-    for (int k = 0; k < BB; ++k) vk[k] = (k < B && valid) ? d.V[((size_t)n * B + k) * Jp + j] : 0.f;
-    float cnt = 0.f;
-    if (valid) cnt = v_tap0 ? 1.f : (float)min(s.Ln[n], J - j);
-
-    float an[BB], ad[BB];
-#pragma unroll
-    for (int k = 0; k < BB; ++k) { an[k] = 0.f; ad[k] = 0.f; }
-    for (int c0 = 0; c0 < F; c0 += FC) {
-        const int nb = min(FC, F - c0);
-        __syncthreads();
-        for (int e = tid; e < nb * B; e += 256) {
-            const int ii = e / B, k = e - ii * B;
-            Ts[e] = d.T[((size_t)(c0 + ii) * N + n) * B + k];
-        }
-        for (int e = tid; e < nb * 2; e += 256) {
-            const int ii = e >> 1, h = e & 1;
-            reinterpret_cast<float4*>(Ps)[e] =
-                reinterpret_cast<const float4*>(d.P + ((size_t)(c0 + ii) * N + n) * Jp + j0)[h];
-        }
-        __syncthreads();
-        if (valid) {
-            for (int ii = ty; ii < nb; ii += 32) {
-                float t[BB];
-                float lam = 0.f;
-#pragma unroll
-                for (int k = 0; k < BB; ++k) {
-                    t[k] = k < B ? Ts[ii * B + k] : 0.f;
-                    lam = fmaf(t[k], vk[k], lam);
-                }
-                const float il = 1.0f / fmaxf(lam, kFloorPsd);
-                const float g = Ps[ii * kFrameTile + tx] * il * il;
-                const float h = cnt * il;
-#pragma unroll
-                for (int k = 0; k < BB; ++k) {
-                    an[k] = fmaf(t[k], g, an[k]);
-                    ad[k] = fmaf(t[k], h, ad[k]);
-                }
-            }
-        }
-    }
-    // reduce over the 4 bin slices inside the warp (lanes with equal tx), then over warps
-#pragma unroll
-    for (int k = 0; k < BB; ++k) {
-        if (k >= B) break;
-        an[k] += __shfl_xor_sync(0xffffffffu, an[k], 8);
-        an[k] += __shfl_xor_sync(0xffffffffu, an[k], 16);
-        ad[k] += __shfl_xor_sync(0xffffffffu, ad[k], 8);
-        ad[k] += __shfl_xor_sync(0xffffffffu, ad[k], 16);
-        if (lane < 8) {
-            red[warp][k][lane] = an[k];
-            red[warp][BB + k][lane] = ad[k];
-        }
-    }
-    __syncthreads();
-    for (int t = tid; t < B * kFrameTile; t += 256) {
-        const int k = t >> 3, x = t & 7;
-        const int jj = j0 + x;
-        float num = 0.f, den = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) { num += red[w][k][x]; den += red[w][BB + k][x]; }
-        float v = 0.f;
-        if (jj < J) {
-            const float vo = d.V[((size_t)n * B + k) * Jp + jj];
-            v = (den > 0.f) ? vo * sqrtf(num / den) : vo;
-            v = fmaxf(v, kFloorNmf);
-            d.V[((size_t)n * B + k) * Jp + jj] = v;
-        }
-        vnew[k][x] = v;
-    }
-    __syncthreads();
-
-    // ---- PSD of the next iteration with the normalised bases
-    const float s0 = s_scale[s.row0[n]];
-    const float t2 = s0 * s0;
-#pragma unroll
-    for (int k = 0; k < BB; ++k) vk[k] = k < B ? vnew[k][tx] : 0.f;
-    for (int c0 = 0; c0 < F; c0 += FC) {
-        const int nb = min(FC, F - c0);
-        if (c0 > 0) {                       // the first chunk is still staged when F <= FC
-            __syncthreads();
-            for (int e = tid; e < nb * B; e += 256) {
-                const int ii = e / B, k = e - ii * B;
-                Ts[e] = d.T[((size_t)(c0 + ii) * N + n) * B + k];
-            }
-            __syncthreads();
-        } else if (F > FC) {
-            __syncthreads();
-            for (int e = tid; e < nb * B; e += 256) {
-                const int ii = e / B, k = e - ii * B;
-                Ts[e] = d.T[((size_t)ii * N + n) * B + k];
-            }
-            __syncthreads();
-        }
-        for (int ii = ty; ii < nb; ii += 32) {
-            float lam = 0.f;
-#pragma unroll
-            for (int k = 0; k < BB; ++k) lam = fmaf(k < B ? Ts[ii * B + k] : 0.f, vk[k], lam);
-            d.invlam[((size_t)(c0 + ii) * N + n) * Jp + j] = valid ? 1.0f / fmaxf(lam * t2, kFloorPsd) : 0.f;
-        }
-    }
+    __shared__ float red_cta[(kFrameThreads / 32) * CTFMNMF_MAX_M];
+    compute_scales(s, d, normalize, s_scale, red_cta);
+    if (blockIdx.x == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
+    const Grp g{(int)threadIdx.x, kFrameThreads, 0};
+    frame_item<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0);
 }
+
+static int frame_fc(const Shape& s, int BB)
+{
+    const int fixed = BB == 4 ? frame_smem_fixed<4>(kFrameThreads)
+                    : BB == 8 ? frame_smem_fixed<8>(kFrameThreads)
+                    : BB == 10 ? frame_smem_fixed<10>(kFrameThreads)
+                    : BB == 16 ? frame_smem_fixed<16>(kFrameThreads) : frame_smem_fixed<32>(kFrameThreads);
+    return frame_chunk(kFrameSmemBytes / 4, s.B, fixed);
+}
+
+static int frame_bb(int B) { return B <= 4 ? 4 : B <= 8 ? 8 : B <= 10 ? 10 : B <= 16 ? 16 : 32; }
 
 // Allow the frame-phase kernels more than 48 KB of shared memory (dynamic + static).
 cudaError_t configure_frame_phase()
@@ -313,6 +173,8 @@ cudaError_t configure_frame_phase()
     cudaError_t e = cudaFuncSetAttribute(frame_phase_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(frame_phase_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(frame_phase_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(frame_phase_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -323,14 +185,18 @@ cudaError_t configure_frame_phase()
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st)
 {
-    const dim3 grid(s.Jp / kFrameTile, s.N);
-    const int FC = frame_chunk_bins(s.B);
+    const int items = (s.Jp / kFrameTile) * s.N;
+    const int BB = frame_bb(s.B);
+    const int FC = frame_fc(s, BB);
     if (FC < 4 || (FC * s.B) % 4 != 0 || s.Jp % kFrameTile != 0) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(float) * (size_t)FC * (s.B + kFrameTile);
-    if (s.B <= 4) frame_phase_kernel<4><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
-    else if (s.B <= 8) frame_phase_kernel<8><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
-    else if (s.B <= 16) frame_phase_kernel<16><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
-    else frame_phase_kernel<32><<<grid, 256, smem, st>>>(s, d, v_tap0, normalize);
+    const size_t smem = kFrameSmemBytes;
+    switch (BB) {
+        case 4: frame_phase_kernel<4><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
+        case 8: frame_phase_kernel<8><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
+        case 10: frame_phase_kernel<10><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
+        case 16: frame_phase_kernel<16><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
+        default: frame_phase_kernel<32><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
+    }
     return cudaGetLastError();
 }
 
@@ -352,13 +218,16 @@ __global__ void finalize_kernel(const Shape s, const State d)
         *w = make_float2(w->x * sc, w->y * sc);
     }
     if (r == 0 && threadIdx.x == 0) {
-        double ls = 0.0;
-        for (int p = 0; p < M; ++p) ls += log((double)d.scale[p]);
-        d.logdet[i] += ls;
+        // fold the running |det| product and the pending row scales into log|det W_i|
+        double f = d.ldm[i];
+        for (int p = 0; p < M; ++p) f *= (double)d.scale[p];
+        d.logdet[i] += log(f) + (double)d.lde[i] * 0.69314718055994530942;
+        d.ldm[i] = 1.0;
+        d.lde[i] = 0;
     }
     if (s.row_l[r] == 0 && threadIdx.x < B) {
         const int n = s.row_n[r];
-        d.T[((size_t)i * N + n) * B + threadIdx.x] *= sc * sc;
+        d.T[(size_t)n * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
     }
 }
 
@@ -531,7 +400,7 @@ __global__ void get_nmf_kernel(const Shape s, const State d, float* __restrict__
             const int k = (int)(e % B);
             const int i = (int)((e / B) % F);
             const int n = (int)(e / ((size_t)B * F));
-            T[e] = d.T[((size_t)i * N + n) * B + k];
+            T[e] = d.T[(size_t)n * s.FBp + (size_t)i * B + k];
         } else {
             const size_t f = e - nT;
             const int j = (int)(f % J);

@@ -1,0 +1,17 @@
+// Persistent kernel instantiations for M = 8 microphones (4 frames per thread).
+#include "persistent_kernel.cuh"
+
+namespace ctf {
+
+const void* persistent_ptr_m8(int BB)
+{
+    switch (BB) {
+        case 4: return reinterpret_cast<const void*>(persistent_kernel<8, 4, 4>);
+        case 8: return reinterpret_cast<const void*>(persistent_kernel<8, 4, 8>);
+        case 10: return reinterpret_cast<const void*>(persistent_kernel<8, 4, 10>);
+        case 16: return reinterpret_cast<const void*>(persistent_kernel<8, 4, 16>);
+    }
+    return nullptr;
+}
+
+}  // namespace ctf

@@ -1,0 +1,522 @@
+// Device code of one CTF-MNMF-ISS iteration, shared by the two-kernel path
+// (bin_phase.cu, kernels.cu) and the persistent kernel (persistent.cu).
+//
+// A "group" is a set of warps of one CTA that works on one bin (bin phase) or one
+// (8-frame tile, source) item (frame phase) and synchronises on its own named barrier.
+//
+// Data written by other CTAs earlier in the same launch (1/lambda, V, T, P, row powers)
+// is read with ld.global.cg (L2, never a possibly stale L1 line).
+#pragma once
+
+#include "internal.cuh"
+
+namespace ctf {
+
+constexpr int kLPad = 8;        // zero frames in front of each staged 1/lambda row (taps <= 8)
+constexpr int kFrameTile = 8;   // frames per frame-phase item
+
+struct Grp {
+    int tid;   // thread index inside the group
+    int nt;    // threads in the group (multiple of 32)
+    int bar;   // named barrier id (0 when the group is the whole CTA)
+};
+
+__device__ __forceinline__ void grp_sync(const Grp& g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(g.bar), "r"(g.nt) : "memory");
+}
+
+__host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
+
+// Warp reduce-scatter of V values (V a power of two <= 32): on return a[0] of lane l holds
+// the warp-wide sum of value index l / (32 / V). log2(V) halving levels exchange half of the
+// remaining values each, then a butterfly finishes the single value.
+template <int V>
+__device__ __forceinline__ void reduce_scatter(float (&a)[V], int lane)
+{
+#pragma unroll
+    for (int lev = 0; (V >> lev) > 1; ++lev) {
+        const int o = 16 >> lev, cnt = V >> lev;
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < cnt / 2; ++q) {
+            const float send = hi ? a[q] : a[q + cnt / 2];
+            const float keep = hi ? a[q + cnt / 2] : a[q];
+            a[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / V; o >= 1; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+}
+
+// ---------------------------------------------------------------------------------------
+// Bin phase: shared memory of a group (floats), ragged sizes rounded so float4 views align
+struct BinSmem {
+    int ils, cw, sq, red, red2, total;   // offsets (floats)
+};
+
+__host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
+{
+    const int NW = nt / 32;
+    BinSmem b;
+    b.ils = 0;                                   // [N][kLPad + Jp]
+    b.cw = b.ils + N * (kLPad + Jp);             // [N][Jp]
+    b.sq = b.cw + N * Jp;                        // [M][Jp]
+    b.red = b.sq + M * Jp;                       // [2][NW][32]   ISS partials
+    b.red2 = b.red + 2 * NW * 32;                // [NW][N][2][32] basis-update partials
+    b.total = b.red2 + NW * N * 2 * 32 + 8;      // + row powers [NW][8] reuse red
+    b.total = (b.total + 3) & ~3;
+    return b;
+}
+
+// One CTF-MNMF-ISS bin update (Sec. III) for bin i by group g.
+//   in:  y  = the bin's rows with the pending normalisation applied (frames g.tid + f*g.nt)
+//        wcol (threads g.tid < M) = column g.tid of W_i with the pending scale applied
+//        scale[r] = pending 1/mu_r (only used for T: T'' = T * scale_{(n,0)}^2)
+//   out: the swept rows and W_i (Eqs. 11-16) stored to Ydst [M][Jp] / Wdst [M][M] (HBM when
+//        GLOBAL, else a shared-memory copy); T[i] by the basis MU (Eq. 17);
+//        P[i] (delayed power, or |y_{(n,0)}|^2 for the tap-0 activation update);
+//        mupart[i][r] = sum_j |y_r(j)|^2;
+//        returns prod_r (1 - z_r), the factor of |det W_i| (Eq. 13).
+template <int M, int FPT, bool GLOBAL, int KB = 16>
+__device__ __forceinline__ float bin_body(const Shape& s, const State& d, const int i, const Grp& g,
+                                          float* gsm, float2 (&y)[M][FPT], float2 (&wcol)[M],
+                                          float2* Ydst, float2* Wdst, const float* scale, const int v_tap0)
+{
+    constexpr int NV = 3 * M - 2;                 // d_p (M real) + n_p, p != r (M-1 complex)
+    constexpr int VP = pow2_at_least(NV);
+    const int J = s.J, Jp = s.Jp, N = s.N, B = s.B;
+    const int LR = kLPad + Jp;
+    const int lane = g.tid & 31, warp = g.tid >> 5, NW = g.nt >> 5;
+    const BinSmem L = bin_smem_layout(M, N, Jp, g.nt);
+    float* ils = gsm + L.ils;
+    float* Cw = gsm + L.cw;
+    float* sq = gsm + L.sq;
+    float* red = gsm + L.red;
+    float* red2 = gsm + L.red2;
+
+    // ---- stage 1/lambda of this bin (cp.async, 16 bytes per copy; zero front pad)
+    {
+        const float4* src = reinterpret_cast<const float4*>(d.invlam + (size_t)i * N * Jp);
+        float4* dst = reinterpret_cast<float4*>(ils);
+        const int LR4 = LR >> 2, J4 = Jp >> 2, P4 = kLPad >> 2;
+        for (int e = g.tid; e < N * LR4; e += g.nt) {
+            const int n = e / LR4, o = e - n * LR4;
+            if (o < P4) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            else cp_async16(dst + e, src + (size_t)n * J4 + o - P4);
+        }
+        cp_async_wait();
+    }
+    grp_sync(g);
+
+    const float invJ = 1.0f / (float)J;
+    float detf = 1.0f;
+    // ---- ISS sweep
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        float a[VP];
+#pragma unroll
+        for (int k = 0; k < VP; ++k) a[k] = 0.f;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = min(g.tid + f * g.nt, Jp - 1);   // frames past Jp hold y = 0
+            const float2 yr = y[r][f];
+            const float pr = abs2(yr);
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                const float ph = ils[s.row_n[p] * LR + kLPad + j - s.row_l[p]];
+                a[p] = fmaf(ph, pr, a[p]);
+                if (p != r) {
+                    const int c = M + 2 * (p - (p > r ? 1 : 0));
+                    const float2 cc = cmul_conj(y[p][f], yr);
+                    a[c] = fmaf(ph, cc.x, a[c]);
+                    a[c + 1] = fmaf(ph, cc.y, a[c + 1]);
+                }
+            }
+        }
+        reduce_scatter<VP>(a, lane);
+        float* rb = red + (r & 1) * NW * 32;
+        if ((lane & (32 / VP - 1)) == 0) rb[warp * 32 + lane / (32 / VP)] = a[0];
+        grp_sync(g);
+        float tk = 0.f;
+        for (int w = 0; w < NW; ++w) tk += rb[w * 32 + (lane & (VP - 1))];
+        float tot[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] = __shfl_sync(0xffffffffu, tk, k);
+        float2 z[M];
+#pragma unroll
+        for (int p = 0; p < M; ++p) {
+            z[p] = make_float2(0.f, 0.f);
+            if (p != r && tot[p] > 0.f) {
+                const int c = M + 2 * (p - (p > r ? 1 : 0));
+                const float inv = 1.0f / tot[p];
+                z[p] = make_float2(tot[c] * inv, tot[c + 1] * inv);
+            }
+        }
+        // 1 - z_r = q^{-1/2}, q = (1/J) sum_j phi_r |y_r|^2: FP32 rsqrt and one Newton step
+        const float q = tot[r] * invJ;
+        float sc = 1.0f;
+        if (q > 0.f) {
+            const float r0 = rsqrtf(q);
+            sc = r0 * fmaf(-0.5f * q * r0, r0, 1.5f);
+        }
+        detf *= sc;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const float2 yr = y[r][f];
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                y[p][f].x -= z[p].x * yr.x - z[p].y * yr.y;
+                y[p][f].y -= z[p].x * yr.y + z[p].y * yr.x;
+            }
+            y[r][f] = make_float2(yr.x * sc, yr.y * sc);
+        }
+        if (g.tid < M) {
+            const float2 wr = wcol[r];
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                wcol[p].x -= z[p].x * wr.x - z[p].y * wr.y;
+                wcol[p].y -= z[p].x * wr.y + z[p].y * wr.x;
+            }
+            wcol[r] = make_float2(wr.x * sc, wr.y * sc);
+        }
+    }
+
+    // ---- store the swept rows and W_i, |y|^2 to shared memory, per-row power partials
+    float rp[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        rp[r] = 0.f;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = g.tid + f * g.nt;
+            if (j < Jp) {
+                const float p2 = abs2(y[r][f]);
+                sq[r * Jp + j] = p2;
+                rp[r] += p2;
+                if (GLOBAL) __stcg(Ydst + (size_t)r * Jp + j, y[r][f]);
+                else Ydst[r * Jp + j] = y[r][f];
+            }
+        }
+    }
+    if (g.tid < M) {
+#pragma unroll
+        for (int p = 0; p < M; ++p) {
+            if (GLOBAL) __stcg(Wdst + p * M + g.tid, wcol[p]);
+            else Wdst[p * M + g.tid] = wcol[p];
+        }
+    }
+    grp_sync(g);
+
+    // ---- delayed power and the basis-update weights at this thread's frames; the
+    //      P/lambda^2 weight overwrites this thread's own 1/lambda entry in place
+    float* Pout = d.P + (size_t)i * N * Jp;
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        if (s.row_l[p] != 0) continue;          // tap-0 rows enumerate the sources
+        const int n = s.row_n[p];
+        const int Lp = s.Ln[n];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = g.tid + f * g.nt;
+            if (j >= Jp) continue;
+            float P = 0.f, cnt = 0.f;
+            if (j < J) {
+                for (int l = 0; l < Lp && j + l < J; ++l) {
+                    P += sq[(p + l) * Jp + j + l];
+                    cnt += 1.f;
+                }
+            }
+            float* wp = ils + n * LR + kLPad + j;
+            const float w = *wp;                // 1/lambda_{n,i,j} (zero past J)
+            *wp = P * w * w;
+            Cw[n * Jp + j] = cnt * w;
+            __stcg(Pout + (size_t)n * Jp + j, v_tap0 ? sq[p * Jp + j] : P);
+        }
+    }
+    grp_sync(g);
+
+    // ---- basis MU (Eq. 17): every thread accumulates num/den of all k over its 4-frame
+    //      columns (float4 loads of V through the L1, which the groups of a CTA share; the
+    //      grid barrier's acquire orders them after the previous frame phase), then a
+    //      reduce-scatter per 16 bases
+    const int J4 = Jp >> 2;
+    for (int n = 0; n < N; ++n) {
+        const float4* A4 = reinterpret_cast<const float4*>(ils + n * LR + kLPad);
+        const float4* C4 = reinterpret_cast<const float4*>(Cw + n * Jp);
+        for (int kb = 0; kb < B; kb += KB) {
+            float a[32];                  // a[k] = numerator, a[16 + k] = denominator of base kb + k
+#pragma unroll
+            for (int k = 0; k < 32; ++k) a[k] = 0.f;
+            const float4* Vn = reinterpret_cast<const float4*>(d.V + ((size_t)n * B + kb) * Jp);
+            for (int q = g.tid; q < J4; q += g.nt) {
+                const float4 A = A4[q], C = C4[q];
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    if (kb + k < B) {
+                        const float4 v = Vn[(size_t)k * J4 + q];
+                        a[k] = fmaf(v.x, A.x, fmaf(v.y, A.y, fmaf(v.z, A.z, fmaf(v.w, A.w, a[k]))));
+                        a[16 + k] = fmaf(v.x, C.x, fmaf(v.y, C.y, fmaf(v.z, C.z, fmaf(v.w, C.w, a[16 + k]))));
+                    }
+                }
+            }
+            reduce_scatter<32>(a, lane);
+            red2[((warp * N + n) * 2 + kb / KB) * 32 + lane] = a[0];
+        }
+    }
+    // row powers for mu: plain warp sums of M values
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        const float v = warp_sum(rp[r]);
+        if (lane == 0) red[warp * 8 + r] = v;          // ISS partial buffers are free now
+    }
+    grp_sync(g);
+    for (int t = g.tid; t < N * B; t += g.nt) {
+        const int n = t / B, k = t - n * B;
+        const int slot = (n * 2 + k / KB) * 32 + (k % KB);
+        float num = 0.f, den = 0.f;
+        for (int w = 0; w < NW; ++w) {
+            num += red2[w * N * 2 * 32 + slot];
+            den += red2[w * N * 2 * 32 + slot + 16];
+        }
+        const float s0 = scale[s.row0[n]];
+        float* Tp = d.T + (size_t)n * s.FBp + (size_t)i * B + k;
+        const float tcur = __ldcg(Tp) * (s0 * s0);
+        const float tn = (den > 0.f) ? tcur * sqrtf(num / den) : tcur;
+        __stcg(Tp, fmaxf(tn, kFloorNmf));
+    }
+    if (g.tid < M) {
+        float t = 0.f;
+        for (int w = 0; w < NW; ++w) t += red[w * 8 + g.tid];
+        __stcg(d.mupart + (size_t)i * M + g.tid, t);
+    }
+    grp_sync(g);     // shared memory is reused by the next item of this group
+    return detf;
+}
+
+// Log-det bookkeeping: |det W_i| is multiplied by `factor` (a product of per-row scales);
+// the running product is kept as mantissa ldm[i] in [0.5, 1) and exponent lde[i] so that
+// no logarithm is taken inside the iteration; fold_logdet() adds log(ldm) + lde log 2.
+__device__ __forceinline__ void logdet_mul(const State& d, int i, double factor)
+{
+    int e = 0;
+    const double m = frexp(__ldcg(d.ldm + i) * factor, &e);
+    d.ldm[i] = m;
+    d.lde[i] = __ldcg(d.lde + i) + e;
+}
+
+// Load bin i's rows (frames g.tid + f*g.nt; zero past Jp) and column g.tid < M of W_i,
+// multiplied by the pending scale. GLOBAL: from HBM/L2 (ld.global.cg), else from a
+// shared-memory copy with the same [M][Jp] / [M][M] layout.
+template <int M, int FPT, bool GLOBAL>
+__device__ __forceinline__ void load_bin(const int Jp, const float2* Ysrc, const float2* Wsrc, const Grp& g,
+                                         const float* scale, float2 (&y)[M][FPT], float2 (&wcol)[M])
+{
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        const float sc = scale[r];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = g.tid + f * g.nt;
+            float2 v = make_float2(0.f, 0.f);
+            if (j < Jp) v = GLOBAL ? __ldcg(Ysrc + (size_t)r * Jp + j) : Ysrc[r * Jp + j];
+            y[r][f] = make_float2(v.x * sc, v.y * sc);
+        }
+    }
+    if (g.tid < M) {
+#pragma unroll
+        for (int p = 0; p < M; ++p) {
+            const float2 w = GLOBAL ? __ldcg(Wsrc + p * M + g.tid) : Wsrc[p * M + g.tid];
+            wcol[p] = make_float2(w.x * scale[p], w.y * scale[p]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Frame phase: one (8-frame tile, source n) item by a group. Shared memory (floats):
+// Ts [FC][B], Ps [FC][8], red [NW][2*BB][8], vnew [BB][8].
+template <int BB>
+__host__ __device__ inline int frame_smem_fixed(int nt) { return (nt / 32) * 2 * BB * kFrameTile + BB * kFrameTile; }
+
+__host__ __device__ inline int frame_chunk(int avail_floats, int B, int fixed)
+{
+    return ((avail_floats - fixed) / (B + kFrameTile)) & ~3;   // multiple of 4: Ps stays 16-byte aligned
+}
+
+// mu_r and the pending scale 1/mu_r from the per-bin row powers (Eq. 19), FP32 tree sums;
+// computed by the whole CTA into scale_out[M] (shared). Uses red_cta[8 * 32] as scratch.
+__device__ __forceinline__ void compute_scales(const Shape& s, const State& d, int normalize,
+                                               float* scale_out, float* red_cta)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int M = s.M, F = s.F;
+    float acc[CTFMNMF_MAX_M];
+#pragma unroll
+    for (int r = 0; r < CTFMNMF_MAX_M; ++r) acc[r] = 0.f;
+    for (int i = tid; i < F; i += blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < CTFMNMF_MAX_M; ++r)
+            if (r < M) acc[r] += __ldcg(d.mupart + (size_t)i * M + r);
+    }
+#pragma unroll
+    for (int r = 0; r < CTFMNMF_MAX_M; ++r) {
+        if (r >= M) break;
+        const float v = warp_sum(acc[r]);
+        if (lane == 0) red_cta[warp * CTFMNMF_MAX_M + r] = v;
+    }
+    __syncthreads();
+    if (tid < M) {
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += red_cta[w * CTFMNMF_MAX_M + tid];
+        const float ms = t / ((float)F * (float)s.J);
+        float sc = 1.0f;
+        if (normalize && ms > 0.f) {
+            const float r0 = rsqrtf(ms);
+            sc = r0 * fmaf(-0.5f * ms * r0, r0, 1.5f);
+        }
+        scale_out[tid] = sc;
+    }
+    __syncthreads();
+}
+
+// Copy `count` contiguous floats of bases (16-byte aligned source; count rounded up to a
+// multiple of 4 stays inside the source block and the staging area) into shared memory.
+__device__ __forceinline__ void stage_bases(const float* src, float* dst, int count, const Grp& g)
+{
+    const int n4 = (count + 3) >> 2;
+    for (int e = g.tid; e < n4; e += g.nt)
+        cp_async16(reinterpret_cast<float4*>(dst) + e, reinterpret_cast<const float4*>(src) + e);
+}
+
+// One frame-phase item (Eq. 18, all-taps form by default, then Eqs. 19-21 for the PSD):
+//   lambda'_{n,i,j} = sum_k T'[i][n][k] V[n][k][j],  T' = the bases of this iteration,
+//   num[k] = sum_i T'[i][n][k] P[i][n][j]/lambda'^2,  den[k] = sum_i T'[i][n][k] c_n(j)/lambda',
+//   V[n][k][j] <- max(V sqrt(num/den), floor),
+//   1/lambda for the next iteration with T'' = T' scale_{(n,0)}^2.
+// Threads: tx = tid & 7 frame of the tile, ty = tid >> 3 bin slice.
+template <int BB>
+__device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
+                                           float* gsm, const int FC, const float* scale, const int v_tap0)
+{
+    const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
+    (void)M;
+    const int ntiles = Jp / kFrameTile;
+    const int n = item / ntiles, tile = item - n * ntiles;
+    const int j0 = tile * kFrameTile;
+    const int tx = g.tid & 7, ty = g.tid >> 3, NY = g.nt >> 3;
+    const int lane = g.tid & 31, warp = g.tid >> 5, NW = g.nt >> 5;
+    const int j = j0 + tx;
+    float* Ts = gsm;                        // [FC][B]
+    float* Ps = gsm + FC * B;               // [FC][8]
+    float* red = Ps + FC * kFrameTile;      // [NW][2*BB][8]
+    float* vnew = red + NW * 2 * BB * kFrameTile;   // [BB][8]
+
+    const bool valid = j < J;
+    float vk[BB];
+#pragma unroll
+    for (int k = 0; k < BB; ++k) vk[k] = (k < B && valid) ? __ldcg(d.V + ((size_t)n * B + k) * Jp + j) : 0.f;
+    const float cnt = valid ? (v_tap0 ? 1.f : (float)min(s.Ln[n], J - j)) : 0.f;
+
+    float an[BB], ad[BB];
+#pragma unroll
+    for (int k = 0; k < BB; ++k) { an[k] = 0.f; ad[k] = 0.f; }
+    const float* Tn = d.T + (size_t)n * s.FBp;
+    for (int c0 = 0; c0 < F; c0 += FC) {
+        const int nb = min(FC, F - c0);
+        stage_bases(Tn + (size_t)c0 * B, Ts, nb * B, g);
+        for (int e = g.tid; e < nb * 2; e += g.nt) {
+            const int ii = e >> 1, h = e & 1;
+            cp_async16(reinterpret_cast<float4*>(Ps) + e,
+                       reinterpret_cast<const float4*>(d.P + ((size_t)(c0 + ii) * N + n) * Jp + j0) + h);
+        }
+        cp_async_wait();
+        grp_sync(g);
+        if (valid) {
+            for (int ii = ty; ii < nb; ii += NY) {
+                const float* Ti = Ts + ii * B;
+                float l0 = 0.f, l1 = 0.f;     // two partial sums: half the dependent chain
+#pragma unroll
+                for (int k = 0; k < BB; k += 2) {
+                    if (k < B) l0 = fmaf(Ti[k], vk[k], l0);
+                    if (k + 1 < BB && k + 1 < B) l1 = fmaf(Ti[k + 1], vk[k + 1], l1);
+                }
+                const float il = recip(fmaxf(l0 + l1, kFloorPsd));
+                const float gg = Ps[ii * kFrameTile + tx] * il * il;
+                const float hh = cnt * il;
+#pragma unroll
+                for (int k = 0; k < BB; ++k) {
+                    if (k < B) {
+                        const float t = Ti[k];
+                        an[k] = fmaf(t, gg, an[k]);
+                        ad[k] = fmaf(t, hh, ad[k]);
+                    }
+                }
+            }
+        }
+        grp_sync(g);
+    }
+    // reduce over the 4 bin slices inside the warp (lanes with equal tx), then over warps
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        if (k >= B) break;
+        an[k] += __shfl_xor_sync(0xffffffffu, an[k], 8);
+        an[k] += __shfl_xor_sync(0xffffffffu, an[k], 16);
+        ad[k] += __shfl_xor_sync(0xffffffffu, ad[k], 8);
+        ad[k] += __shfl_xor_sync(0xffffffffu, ad[k], 16);
+        if (lane < 8) {
+            red[(warp * 2 * BB + k) * kFrameTile + lane] = an[k];
+            red[(warp * 2 * BB + BB + k) * kFrameTile + lane] = ad[k];
+        }
+    }
+    grp_sync(g);
+    for (int t = g.tid; t < B * kFrameTile; t += g.nt) {
+        const int k = t >> 3, x = t & 7;
+        const int jj = j0 + x;
+        float num = 0.f, den = 0.f;
+        for (int w = 0; w < NW; ++w) {
+            num += red[(w * 2 * BB + k) * kFrameTile + x];
+            den += red[(w * 2 * BB + BB + k) * kFrameTile + x];
+        }
+        float v = 0.f;
+        if (jj < J) {
+            float* Vp = d.V + ((size_t)n * B + k) * Jp + jj;
+            const float vo = __ldcg(Vp);
+            v = (den > 0.f) ? vo * sqrtf(num / den) : vo;
+            v = fmaxf(v, kFloorNmf);
+            __stcg(Vp, v);
+        }
+        vnew[k * kFrameTile + x] = v;
+    }
+    grp_sync(g);
+
+    // ---- PSD of the next iteration with the normalised bases
+    const float s0 = scale[s.row0[n]];
+    const float t2 = s0 * s0;
+#pragma unroll
+    for (int k = 0; k < BB; ++k) vk[k] = k < B ? vnew[k * kFrameTile + tx] : 0.f;
+    for (int c0 = 0; c0 < F; c0 += FC) {
+        const int nb = min(FC, F - c0);
+        if (F > FC) {                      // restage the bases chunk (only when chunked)
+            stage_bases(Tn + (size_t)c0 * B, Ts, nb * B, g);
+            cp_async_wait();
+            grp_sync(g);
+        }
+        for (int ii = ty; ii < nb; ii += NY) {
+            const float* Ti = Ts + ii * B;
+            float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < BB; k += 2) {
+                if (k < B) l0 = fmaf(Ti[k], vk[k], l0);
+                if (k + 1 < BB && k + 1 < B) l1 = fmaf(Ti[k + 1], vk[k + 1], l1);
+            }
+            __stcg(d.invlam + ((size_t)(c0 + ii) * N + n) * Jp + j,
+                   valid ? recip(fmaxf((l0 + l1) * t2, kFloorPsd)) : 0.f);
+        }
+        if (F > FC) grp_sync(g);
+    }
+    grp_sync(g);     // shared memory is reused by the next item of this group
+}
+
+}  // namespace ctf

@@ -11,7 +11,7 @@ import pytest
 
 from paper_2510_02382_gb300 import synth
 
-from gpu_helpers import cost_close, rel_fro, run_gpu, run_oracle
+from gpu_helpers import cost_close, make_solver, rel_fro, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -42,22 +42,27 @@ SHAPES = [
 ]
 
 
+PATHS = ["two_kernel", "persistent"]
+
+
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"M{s[0]}N{s[1]}F{s[3]}J{s[4]}B{s[5]}")
-def test_one_iteration_matches_oracle(shape):
+def test_one_iteration_matches_oracle(shape, path):
     M, N, Ln, F, J, B = shape
     mix = synth.random_case(1000 + M * 7 + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
-    g = run_gpu(mix, 1)
+    g = run_gpu(mix, 1, path=path)
     r = run_oracle(mix, 1)
     _check_state(g, r, mix)
     ok, err = cost_close(g["cost"], r["cost"], 1e-5, F, J, M)
     assert ok, err
 
 
-@pytest.mark.parametrize("shape", SHAPES[:5], ids=lambda s: f"M{s[0]}F{s[3]}J{s[4]}")
-def test_ten_iterations_cost(shape):
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("shape", SHAPES[:5] + SHAPES[9:10], ids=lambda s: f"M{s[0]}F{s[3]}J{s[4]}")
+def test_ten_iterations_cost(shape, path):
     M, N, Ln, F, J, B = shape
     mix = synth.random_case(2000 + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
-    g = run_gpu(mix, 10)
+    g = run_gpu(mix, 10, path=path)
     r = run_oracle(mix, 10)
     ok, err = cost_close(g["cost"], r["cost"], 1e-5, F, J, M)
     assert ok, err
@@ -74,10 +79,11 @@ def test_c1_workload_10_iterations():
     assert ok, err
 
 
-def test_tap0_activation_update_and_no_normalisation():
+@pytest.mark.parametrize("path", PATHS)
+def test_tap0_activation_update_and_no_normalisation(path):
     mix = synth.random_case(77, M=4, N=2, F=5, J=300, B=4, Ln=(2, 2))
     for v_mode, norm in [("tap0", True), ("all_taps", False), ("tap0", False)]:
-        g = run_gpu(mix, 3, v_mode=v_mode, normalize=norm)
+        g = run_gpu(mix, 3, v_mode=v_mode, normalize=norm, path=path)
         r = run_oracle(mix, 3, v_mode=v_mode, normalize=norm)
         assert rel_fro(g["y"], r["y"]) < 1e-4, (v_mode, norm)
         ok, err = cost_close(g["cost"], r["cost"], 1e-5, 5, 300, 4)
@@ -86,9 +92,62 @@ def test_tap0_activation_update_and_no_normalisation():
 
 def test_graph_and_stream_launches_agree():
     mix = synth.random_case(5, M=3, N=2, F=6, J=100, B=4, Ln=(2, 1))
-    a = run_gpu(mix, 4, use_graph=True)
-    b = run_gpu(mix, 4, use_graph=False)
+    a = run_gpu(mix, 4, use_graph=True, path="two_kernel")
+    b = run_gpu(mix, 4, use_graph=False, path="two_kernel")
     assert np.array_equal(a["y"], b["y"]) and a["cost"] == b["cost"]
+
+
+@pytest.mark.parametrize("shape", [(3, 2, (2, 1), 40, 600, 10), (4, 3, (2, 1, 1), 9, 1500, 16),
+                                   (6, 2, (3, 3), 5, 300, 3)], ids=lambda s: f"M{s[0]}J{s[4]}")
+def test_persistent_and_two_kernel_paths_agree(shape):
+    """Same equations, different reduction trees: the two paths agree to FP32 rounding."""
+    M, N, Ln, F, J, B = shape
+    mix = synth.random_case(4000 + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+    a = run_gpu(mix, 5, path="persistent")
+    b = run_gpu(mix, 5, path="two_kernel")
+    assert rel_fro(a["y"], b["y"]) < 1e-5 and rel_fro(a["V"], b["V"]) < 1e-5
+    ok, err = cost_close(a["cost"], b["cost"], 1e-6, F, J, M)
+    assert ok, err
+
+
+def test_auto_path_selection():
+    mix = synth.make_mixture(synth.CONFIGS["C2"])
+    s = make_solver(mix)
+    assert s.path == "persistent"
+    s.close()
+    mix = synth.random_case(1, M=3, N=2, F=4, J=64, B=20, Ln=(2, 1))   # B > 16: two-kernel only
+    s = make_solver(mix)
+    assert s.path == "two_kernel"
+    s.close()
+
+
+def test_bounded_barrier_wait_reports_timeout_and_recovers():
+    """One thread block skips its first grid-barrier arrival (host-set test hook): every
+    other block's bounded wait runs out, the launch ends, ctfmnmf_synchronize reports
+    ETIMEOUT, and after a reload the handle solves correctly again."""
+    import torch
+    from paper_2510_02382_gb300.api import CtfMnmfError
+    mix = synth.random_case(8, M=3, N=2, F=20, J=200, B=4, Ln=(2, 1))
+    s = make_solver(mix, path="persistent", wait_timeout_ms=100)
+    X = torch.from_numpy(mix.X).cuda()
+    T0, V0 = torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda()
+    s.load_stft(X)
+    s.set_init(T0, V0)
+    s.debug_skip_arrival(0)
+    s.iterate(3)
+    with pytest.raises(CtfMnmfError) as e:
+        s.synchronize()
+    assert e.value.name == "ETIMEOUT"
+    with pytest.raises(CtfMnmfError) as e:
+        s.iterate(1)
+    assert e.value.name == "ESTATE"
+    s.load_stft(X)
+    s.set_init(T0, V0)
+    s.iterate(3)
+    s.synchronize()
+    r = run_oracle(mix, 3)
+    assert rel_fro(s.get_demixed().cpu().numpy(), r["y"]) < 1e-4
+    s.close()
 
 
 def test_repeated_iterate_calls_compose():
@@ -99,7 +158,7 @@ def test_repeated_iterate_calls_compose():
     sp = mix.spec
     outs = []
     for split in [(4,), (2, 2), (1, 3)]:
-        s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln)
+        s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln, path="two_kernel")
         s.load_stft(torch.from_numpy(mix.X).cuda())
         s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
         for k in split:
@@ -190,27 +249,30 @@ def test_host_buffers_match_device_buffers():
 
 # ---- full-size workloads (the benchmark's launch configuration)
 
-def test_c2_full_size_1_and_10_iterations():
+@pytest.mark.parametrize("path", PATHS)
+def test_c2_full_size_1_and_10_iterations(path):
     mix = synth.make_mixture(synth.CONFIGS["C2"])
     sp = mix.spec
-    g, r = run_gpu(mix, 1), run_oracle(mix, 1)
+    g, r = run_gpu(mix, 1, path=path), run_oracle(mix, 1)
     assert rel_fro(g["y"], r["y"]) < 1e-4, rel_fro(g["y"], r["y"])
-    g, r = run_gpu(mix, 10), run_oracle(mix, 10)
+    g, r = run_gpu(mix, 10, path=path), run_oracle(mix, 10)
     ok, err = cost_close(g["cost"], r["cost"], 1e-5, sp.F, sp.J, sp.M)
     assert ok, err
 
 
-def test_c2_full_size_100_iterations_cost():
+@pytest.mark.parametrize("path", PATHS)
+def test_c2_full_size_100_iterations_cost(path):
     mix = synth.make_mixture(synth.CONFIGS["C2"])
     sp = mix.spec
-    g, r = run_gpu(mix, 100), run_oracle(mix, 100)
+    g, r = run_gpu(mix, 100, path=path), run_oracle(mix, 100)
     ok, err = cost_close(g["cost"], r["cost"], 1e-3, sp.F, sp.J, sp.M)
     assert ok, err
 
 
-def test_c3_full_size_1_iteration():
+@pytest.mark.parametrize("path", PATHS)
+def test_c3_full_size_1_iteration(path):
     mix = synth.make_mixture(synth.CONFIGS["C3"])
-    g, r = run_gpu(mix, 1), run_oracle(mix, 1)
+    g, r = run_gpu(mix, 1, path=path), run_oracle(mix, 1)
     assert rel_fro(g["y"], r["y"]) < 1e-4, rel_fro(g["y"], r["y"])
     sp = mix.spec
     ok, err = cost_close(g["cost"], r["cost"], 1e-5, sp.F, sp.J, sp.M)
