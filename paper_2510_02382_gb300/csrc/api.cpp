@@ -211,7 +211,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         {(void**)&d.cost_out, sizeof(double)},
         {(void**)&d.ldm, sizeof(double) * F},
         {(void**)&d.lde, sizeof(int) * F},
-        {(void**)&d.sync, sizeof(unsigned) * (32 + ctf::kMaxPersistCtas)},
+        {(void**)&d.sync, sizeof(unsigned) * 32},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -227,7 +227,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         rc = CTFMNMF_ECUDA;
     }
     if (rc == CTFMNMF_OK && (cudaMemset(d.flag, 0, sizeof(int) * 4) != cudaSuccess ||
-                             cudaMemset(d.sync, 0, sizeof(unsigned) * (32 + ctf::kMaxPersistCtas)) != cudaSuccess ||
+                             cudaMemset(d.sync, 0, sizeof(unsigned) * 32) != cudaSuccess ||
                              cudaMemset(d.P, 0, sizeof(float) * FNJ) != cudaSuccess ||
                              cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
         rc = CTFMNMF_ECUDA;

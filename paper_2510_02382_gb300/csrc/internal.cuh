@@ -23,7 +23,6 @@
 
 namespace ctf {
 
-constexpr int kMaxPersistCtas = 1024; // grid barrier flags reserved per handle
 constexpr float kFloorNmf = 1e-12f;   // floor of T and V after each multiplicative update
 constexpr float kFloorPsd = 1e-18f;   // floor of lambda where it is formed
 
@@ -48,7 +47,7 @@ struct State {
     float* scale;
     double* ldm;        // [F] mantissa of the log-det product not yet folded into logdet
     int* lde;           // [F] its binary exponent
-    unsigned* sync;     // [32 + kMaxPersistCtas] grid barrier: [0] abort word, [32 + b] flag of CTA b
+    unsigned* sync;     // grid barrier words: [0] abort, [1] arrivals, [2] generation
     int* flag;          // [0]: non-finite input seen, [1]: device wait timed out
     double* cost_part;  // [F] per-bin cost
     double* cost_out;   // [1]

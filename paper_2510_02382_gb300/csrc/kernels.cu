@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape 
     compute_scales(s, d, normalize, s_scale, red_cta);
     if (blockIdx.x == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
     const Grp g{(int)threadIdx.x, kFrameThreads, 0};
-    frame_item<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0);
+    if constexpr (BB <= 16) frame_item<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0);
+    else frame_item_wide<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0);
 }
 
 static int frame_fc(const Shape& s, int BB)

@@ -72,9 +72,7 @@ PersistPlan plan_persistent(const Shape& s)
                 cudaGetLastError();
                 continue;
             }
-            int ctas = per_sm * sms;
-            if (ctas > kMaxPersistCtas) ctas = kMaxPersistCtas;
-            if (ctas > nt) ctas = nt;               // every CTA polls all flags, one per thread
+            const int ctas = per_sm * sms;
             if (resident && (long long)ctas * groups < s.F) continue;
             p.groups = groups;
             p.gsm = gsm;
@@ -97,9 +95,9 @@ cudaError_t launch_persistent(const Shape& s, const State& d, const PersistPlan&
     if (!p.ok) return cudaErrorInvalidValue;
     const void* k = select_kernel(s.M, persist_bb(s.B));
     if (!k || s.Jp % 8 != 0 || (p.fc * s.B) % 4 != 0) return cudaErrorInvalidValue;
-    // reset the abort word and the per-CTA barrier flags (epochs restart at 1 every launch)
-    if (p.ctas > kMaxPersistCtas) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(d.sync, 0, (32 + kMaxPersistCtas) * sizeof(unsigned), st);
+    // reset the barrier words (epochs restart at 1 every launch; an aborted launch may have
+    // left the abort word set)
+    cudaError_t e = cudaMemsetAsync(d.sync, 0, 32 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     PersistArgs pa;
     pa.n_iter = n_iter;

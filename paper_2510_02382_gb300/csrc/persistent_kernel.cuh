@@ -36,41 +36,51 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid barrier with one flag word per CTA: CTA b publishes the barrier's epoch in
-// flags[b] (release), then threads t < gridDim.x of every CTA poll flags[t] (acquire) until
-// it reaches the epoch, so no word takes more than one writer. Every poll is bounded by
-// the timeout; a CTA whose poll runs out sets the timeout status and the abort word, and
-// every CTA leaves at its next barrier. Returns false (uniformly in the CTA) on abort.
-// sync[0] = abort word; flags = sync + 32 (one per CTA).
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier: thread 0 of every CTA fences its CTA's writes and adds 1 to an arrival
+// counter that is never reset within a launch; the CTA whose arrival completes barrier
+// number `epoch` (counter = epoch * gridDim.x) publishes `epoch` in the generation word
+// (release), the others poll it with relaxed loads and fence once it has moved. Every
+// poll is bounded by the timeout; a CTA whose poll runs out sets the timeout status and
+// the abort word, and every CTA leaves at its next barrier. Returns false (uniformly in
+// the CTA) on abort. Words: sync[0] abort, sync[1] arrivals, sync[2] generation.
 __device__ __forceinline__ bool grid_sync(const State& d, unsigned epoch, unsigned long long timeout_ns,
                                           bool skip_arrival)
 {
     __shared__ int s_ok2[2];                          // by epoch parity: no reuse race
     int& s_ok = s_ok2[epoch & 1u];
     unsigned* abort_word = d.sync;
-    unsigned* flags = d.sync + 32;
-    if (threadIdx.x == 0) s_ok = 1;
-    __syncthreads();                                  // all of this CTA's writes precede the flag
+    unsigned* count = d.sync + 1;
+    unsigned* gen = d.sync + 2;
+    __syncthreads();                                  // all of this CTA's writes precede the arrival
     if (threadIdx.x == 0) {
-        __threadfence();
-        if (!skip_arrival) st_release(flags + blockIdx.x, epoch);
-    }
-    if (threadIdx.x < gridDim.x) {
-        const unsigned* f = flags + threadIdx.x;
-        if (ld_acquire(f) < epoch) {
-            const unsigned long long t0 = global_ns();
-            while (ld_acquire(f) < epoch) {
-                if (ld_acquire(abort_word) != 0u) { s_ok = 0; break; }
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicOr(d.flag + 1, 1);
-                    atomicExch(abort_word, 1u);
-                    s_ok = 0;
-                    break;
+        int ok = ld_relaxed(abort_word) == 0u;
+        if (ok) {
+            __threadfence();
+            const unsigned arrived = skip_arrival ? 0u : atomicAdd(count, 1u) + 1u;
+            if (arrived == epoch * gridDim.x) {
+                st_release(gen, epoch);
+            } else {
+                const unsigned long long t0 = global_ns();
+                while (ld_relaxed(gen) < epoch) {
+                    if (ld_relaxed(abort_word) != 0u) { ok = 0; break; }
+                    if (global_ns() - t0 > timeout_ns) {
+                        atomicOr(d.flag + 1, 1);
+                        atomicExch(abort_word, 1u);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
+            __threadfence();
         }
-        __threadfence();
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -141,7 +151,11 @@ persistent_kernel(const Shape s, const State d, const PersistArgs pa)
         // ---- normalisation scale and frame items
         compute_scales(s, d, pa.normalize, s_new, red_cta);
         for (int item = blockIdx.x; item < items; item += gridDim.x)
-            frame_item<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0);
+        {
+            // two frames per thread where the registers allow it (128 per thread here)
+            if constexpr (BB <= 10) frame_item<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0);
+            else frame_item_wide<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0);
+        }
         alive = grid_sync(d, 2u * it + 2u, pa.timeout_ns, false);
         if (threadIdx.x < CTFMNMF_MAX_M) s_old[threadIdx.x] = s_new[threadIdx.x];
         __syncthreads();

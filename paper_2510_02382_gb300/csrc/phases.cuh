@@ -395,9 +395,10 @@ __device__ __forceinline__ void stage_bases(const float* src, float* dst, int co
 //   num[k] = sum_i T'[i][n][k] P[i][n][j]/lambda'^2,  den[k] = sum_i T'[i][n][k] c_n(j)/lambda',
 //   V[n][k][j] <- max(V sqrt(num/den), floor),
 //   1/lambda for the next iteration with T'' = T' scale_{(n,0)}^2.
-// Threads: tx = tid & 7 frame of the tile, ty = tid >> 3 bin slice.
+// Threads: tx = tid & 7 frame of the tile, ty = tid >> 3 bin slice (one frame per thread:
+// the variant for many bases, BB = 32).
 template <int BB>
-__device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
+__device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, const int item, const Grp& g,
                                            float* gsm, const int FC, const float* scale, const int v_tap0)
 {
     const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
@@ -513,6 +514,157 @@ __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const
             }
             __stcg(d.invlam + ((size_t)(c0 + ii) * N + n) * Jp + j,
                    valid ? recip(fmaxf((l0 + l1) * t2, kFloorPsd)) : 0.f);
+        }
+        if (F > FC) grp_sync(g);
+    }
+    grp_sync(g);     // shared memory is reused by the next item of this group
+}
+
+// The same item with two frames per thread (BB <= 16): each row of bases read from shared
+// memory feeds the two frames' PSD and both sums, and the reduction over the 8 bin slices
+// of a warp is a three-level reduce-scatter. Threads: tx = tid & 3 owns frames j0 + 2tx
+// and j0 + 2tx + 1, ty = tid >> 2 is the bin slice.
+template <int BB>
+__device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
+                                           float* gsm, const int FC, const float* scale, const int v_tap0)
+{
+    static_assert(BB % 2 == 0 && BB <= 16, "two-frame item needs an even BB <= 16");
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
+    const int ntiles = Jp / kFrameTile;
+    const int n = item / ntiles, tile = item - n * ntiles;
+    const int j0 = tile * kFrameTile;
+    const int tx = g.tid & 3, ty = g.tid >> 2, NY = g.nt >> 2;
+    const int lane = g.tid & 31, warp = g.tid >> 5, NW = g.nt >> 5;
+    const int ja = j0 + 2 * tx;
+    float* Ts = gsm;                                // [FC][B]
+    float* Ps = gsm + FC * B;                       // [FC][8]
+    float* red = Ps + FC * kFrameTile;              // [NW][4 frame pairs][4 BB]
+    float* vnew = red + NW * 16 * BB;               // [BB][8]
+
+    const bool va = ja < J, vb = ja + 1 < J;
+    float v0[BB], v1[BB];
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        float2 v = make_float2(0.f, 0.f);
+        if (k < B) v = __ldcg(reinterpret_cast<const float2*>(d.V + ((size_t)n * B + k) * Jp + ja));
+        v0[k] = va ? v.x : 0.f;
+        v1[k] = vb ? v.y : 0.f;
+    }
+    const int Lp = s.Ln[n];
+    const float c0 = va ? (v_tap0 ? 1.f : (float)min(Lp, J - ja)) : 0.f;
+    const float c1 = vb ? (v_tap0 ? 1.f : (float)min(Lp, J - ja - 1)) : 0.f;
+
+    float acc[4 * BB];        // numerators of frames 0, 1 then denominators of frames 0, 1
+#pragma unroll
+    for (int k = 0; k < 4 * BB; ++k) acc[k] = 0.f;
+    const float* Tn = d.T + (size_t)n * s.FBp;
+    for (int cb = 0; cb < F; cb += FC) {
+        const int nb = min(FC, F - cb);
+        stage_bases(Tn + (size_t)cb * B, Ts, nb * B, g);
+        for (int e = g.tid; e < nb * 2; e += g.nt) {
+            const int ii = e >> 1, h = e & 1;
+            cp_async16(reinterpret_cast<float4*>(Ps) + e,
+                       reinterpret_cast<const float4*>(d.P + ((size_t)(cb + ii) * N + n) * Jp + j0) + h);
+        }
+        cp_async_wait();
+        grp_sync(g);
+        for (int ii = ty; ii < nb; ii += NY) {
+            const float* Ti = Ts + ii * B;
+            float t[BB];
+#pragma unroll
+            for (int k = 0; k < BB; ++k) t[k] = k < B ? Ti[k] : 0.f;
+            float l0a = 0.f, l0b = 0.f, l1a = 0.f, l1b = 0.f;
+#pragma unroll
+            for (int k = 0; k < BB; k += 2) {
+                l0a = fmaf(t[k], v0[k], l0a);
+                l0b = fmaf(t[k + 1], v0[k + 1], l0b);
+                l1a = fmaf(t[k], v1[k], l1a);
+                l1b = fmaf(t[k + 1], v1[k + 1], l1b);
+            }
+            const float i0 = recip(fmaxf(l0a + l0b, kFloorPsd));
+            const float i1 = recip(fmaxf(l1a + l1b, kFloorPsd));
+            const float2 p = *reinterpret_cast<const float2*>(Ps + ii * kFrameTile + 2 * tx);
+            const float g0 = p.x * i0 * i0, g1 = p.y * i1 * i1, h0 = c0 * i0, h1 = c1 * i1;
+#pragma unroll
+            for (int k = 0; k < BB; ++k) {
+                acc[k] = fmaf(t[k], g0, acc[k]);
+                acc[BB + k] = fmaf(t[k], g1, acc[BB + k]);
+                acc[2 * BB + k] = fmaf(t[k], h0, acc[2 * BB + k]);
+                acc[3 * BB + k] = fmaf(t[k], h1, acc[3 * BB + k]);
+            }
+        }
+        grp_sync(g);
+    }
+    // sum over the 8 bin slices of the warp (lane bits 2..4): three halving levels; lane
+    // then holds BB/2 consecutive values starting at `base` for its frame pair tx
+#pragma unroll
+    for (int lev = 0; lev < 3; ++lev) {
+        const int o = 16 >> lev, half = (2 * BB) >> lev;
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const float send = hi ? acc[q] : acc[q + half];
+            const float keep = hi ? acc[q + half] : acc[q];
+            acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    {
+        const int base = ((lane >> 4) & 1) * 2 * BB + ((lane >> 3) & 1) * BB + ((lane >> 2) & 1) * (BB / 2);
+        float* rw = red + (warp * 4 + tx) * 4 * BB + base;
+#pragma unroll
+        for (int q = 0; q < BB / 2; ++q) rw[q] = acc[q];
+    }
+    grp_sync(g);
+    for (int t = g.tid; t < B * kFrameTile; t += g.nt) {
+        const int k = t >> 3, x = t & 7;
+        const int jj = j0 + x;
+        const int off = (x >> 1) * 4 * BB + (x & 1) * BB + k;
+        float num = 0.f, den = 0.f;
+        for (int w = 0; w < NW; ++w) {
+            num += red[w * 16 * BB + off];
+            den += red[w * 16 * BB + off + 2 * BB];
+        }
+        float v = 0.f;
+        if (jj < J) {
+            float* Vp = d.V + ((size_t)n * B + k) * Jp + jj;
+            const float vo = __ldcg(Vp);
+            v = (den > 0.f) ? vo * sqrtf(num / den) : vo;
+            v = fmaxf(v, kFloorNmf);
+            __stcg(Vp, v);
+        }
+        vnew[k * kFrameTile + x] = v;
+    }
+    grp_sync(g);
+
+    // ---- PSD of the next iteration with the normalised bases (two frames per thread)
+    const float s0 = scale[s.row0[n]];
+    const float t2 = s0 * s0;
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        v0[k] = k < B ? vnew[k * kFrameTile + 2 * tx] : 0.f;
+        v1[k] = k < B ? vnew[k * kFrameTile + 2 * tx + 1] : 0.f;
+    }
+    for (int cb = 0; cb < F; cb += FC) {
+        const int nb = min(FC, F - cb);
+        if (F > FC) {                      // restage the bases chunk (only when chunked)
+            stage_bases(Tn + (size_t)cb * B, Ts, nb * B, g);
+            cp_async_wait();
+            grp_sync(g);
+        }
+        for (int ii = ty; ii < nb; ii += NY) {
+            const float* Ti = Ts + ii * B;
+            float l0a = 0.f, l0b = 0.f, l1a = 0.f, l1b = 0.f;
+#pragma unroll
+            for (int k = 0; k < BB; k += 2) {
+                const float ta = k < B ? Ti[k] : 0.f, tb = k + 1 < B ? Ti[k + 1] : 0.f;
+                l0a = fmaf(ta, v0[k], l0a);
+                l0b = fmaf(tb, v0[k + 1], l0b);
+                l1a = fmaf(ta, v1[k], l1a);
+                l1b = fmaf(tb, v1[k + 1], l1b);
+            }
+            const float2 o = make_float2(va ? recip(fmaxf((l0a + l0b) * t2, kFloorPsd)) : 0.f,
+                                         vb ? recip(fmaxf((l1a + l1b) * t2, kFloorPsd)) : 0.f);
+            __stcg(reinterpret_cast<float2*>(d.invlam + ((size_t)(cb + ii) * N + n) * Jp + ja), o);
         }
         if (F > FC) grp_sync(g);
     }
