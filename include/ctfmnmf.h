@@ -195,6 +195,29 @@ int ctfmnmf_get_logdet(ctfmnmf_t h, double* logdet);
 /* NMF factors: device pointers, float32 T [N][F][B] and V [N][B][J]; either may be NULL. */
 int ctfmnmf_get_nmf(ctfmnmf_t h, float* T, float* V);
 
+/*
+ * ctfmnmf_cost_noalloc -- the negative log-likelihood of Eq. 5 (as ctfmnmf_cost) from
+ * caller-held buffers, without allocating any device memory. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc where they need the
+ * cost, e.g. code that runs while a CUDA graph is being captured on its stream, code inside
+ * an allocator or memory-pool callback, or an application whose device memory is owned by
+ * another framework.
+ *   Y [M][F][J] complex64, T [N][F][B] and V [N][B][J] float32, logdet [F] float64: device
+ *   pointers in the layouts of ctfmnmf_get_demixed / _get_nmf / _get_logdet (read only);
+ *   Ln[N]: host array of taps (sum M); out: device pointer to one double (written);
+ *   stream: cudaStream_t (NULL = legacy default stream). Asynchronous.
+ * Limit: F <= 16384 bins (EINVAL beyond, with a message from ctfmnmf_last_error(NULL)).
+ * Scratch: the per-bin partial sums live in a 128 KiB static device array that every GPU
+ * loading the library holds until exit. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. All calls share the array: calls whose kernels overlap on the GPU
+ * (different streams or threads without ordering) race and give wrong results.
+ * Errors: EINVAL (dimensions, taps, null pointers, F too large), ECUDA (launch failed).
+ */
+int ctfmnmf_cost_noalloc(int M, int N, const int* Ln, int B, int F, int J, const void* Y,
+                         const float* T, const float* V, const double* logdet, double* out,
+                         void* stream);
+
 /* ---- diagnostics (not part of the method) ---- */
 
 /*

@@ -66,6 +66,8 @@ _SIGS = {
     "ctfmnmf_get_path": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_time_persistent": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_debug_skip_arrival": (c_int, [c_void_p, c_int]),
+    "ctfmnmf_cost_noalloc": (c_int, [c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 
@@ -99,6 +101,22 @@ def _ptr(t) -> Optional[int]:
     if t is None:
         return None
     return t.data_ptr()
+
+
+def cost_noalloc(Y, T, V, logdet, Ln, out, stream=None):
+    """ctfmnmf_cost_noalloc: Eq. 5 from caller-held device tensors into `out` (one float64 on
+    the device), without any device allocation by the library. Y [M][F][J] complex64,
+    T [N][F][B], V [N][B][J] float32, logdet [F] float64."""
+    import torch
+    M, F, J = Y.shape
+    N, _, B = T.shape
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ln_arr = (c_int * N)(*Ln)
+    rc = lib().ctfmnmf_cost_noalloc(M, N, ln_arr, B, F, J, c_void_p(Y.data_ptr()), c_void_p(T.data_ptr()),
+                                    c_void_p(V.data_ptr()), c_void_p(logdet.data_ptr()),
+                                    c_void_p(out.data_ptr()), c_void_p(st.cuda_stream))
+    _check(rc, None)
+    return out
 
 
 class CTFMNMF:

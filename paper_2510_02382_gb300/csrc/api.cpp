@@ -117,6 +117,11 @@ long long iteration_kernels(int n_iter) { return 2LL * n_iter + kFinalizeKernels
 
 }  // namespace
 
+void ctf::set_thread_error(const char* msg)
+{
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+}
+
 extern "C" {
 
 void ctfmnmf_default_options(ctfmnmf_options* opt)

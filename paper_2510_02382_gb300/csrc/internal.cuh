@@ -88,6 +88,9 @@ cudaError_t launch_persistent(const Shape& s, const State& d, const PersistPlan&
                               int v_tap0, int normalize, unsigned long long timeout_ns, int skip_cta,
                               cudaStream_t st);
 
+// Set the message that ctfmnmf_last_error(NULL) returns on this thread.
+void set_thread_error(const char* msg);
+
 // Frames per thread / threads per block chosen for the bin phase; false if unsupported.
 bool bin_phase_config(int M, int J, int* fpt, int* threads);
 size_t bin_phase_smem(const Shape& s);
