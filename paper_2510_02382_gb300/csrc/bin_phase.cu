@@ -61,9 +61,9 @@ static cudaError_t launch_mf(const Shape& s, const State& d, int v_tap0, int nt,
                              bool configure_only)
 {
     // 8 frames per thread: up to 512 threads, 128 registers; otherwise 256 threads and
-    // 4 CTAs per SM (64 registers) when the bin's samples take at most 24 registers
+    // 4 CTAs per SM (64 registers) for 4 frames per thread and M <= 3, else 2 CTAs per SM
     constexpr int kMaxT = FPT == 8 ? 512 : 256;
-    constexpr int kMinB = FPT == 8 ? 1 : (M * FPT >= 16 ? 2 : 4);
+    constexpr int kMinB = FPT == 8 ? 1 : ((FPT == 4 && M * FPT < 16) ? 4 : 2);
     if (configure_only) {
         // the device's opt-in maximum, so that handles of different J share the setting
         int dev = 0, optin = 0;

@@ -109,6 +109,20 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
     }
     grp_sync(g);
 
+    // delayed weights phi_p(j) = 1/lambda_{n(p),i,j-l(p)} (zero for j < l(p)): kept in
+    // registers when they fit beside the rows, else read from shared memory at each use
+    constexpr bool kPhiReg = M * FPT <= 24;
+    constexpr int PR = kPhiReg ? M : 1, PF = kPhiReg ? FPT : 1;
+    float phi[PR][PF];
+    if constexpr (kPhiReg) {
+#pragma unroll
+        for (int p = 0; p < M; ++p) {
+            const float* row = ils + s.row_n[p] * LR + kLPad - s.row_l[p];
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) phi[p % PR][f % PF] = row[min(g.tid + f * g.nt, Jp - 1)];  // y = 0 past Jp
+        }
+    }
+
     const float invJ = 1.0f / (float)J;
     float detf = 1.0f;
     // ---- ISS sweep
@@ -119,12 +133,12 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         for (int k = 0; k < VP; ++k) a[k] = 0.f;
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
-            const int j = min(g.tid + f * g.nt, Jp - 1);   // frames past Jp hold y = 0
             const float2 yr = y[r][f];
             const float pr = abs2(yr);
 #pragma unroll
             for (int p = 0; p < M; ++p) {
-                const float ph = ils[s.row_n[p] * LR + kLPad + j - s.row_l[p]];
+                const float ph = kPhiReg ? phi[p % PR][f % PF]
+                                         : ils[s.row_n[p] * LR + kLPad + min(g.tid + f * g.nt, Jp - 1) - s.row_l[p]];
                 a[p] = fmaf(ph, pr, a[p]);
                 if (p != r) {
                     const int c = M + 2 * (p - (p > r ? 1 : 0));
@@ -223,8 +237,9 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
             const int j = g.tid + f * g.nt;
             if (j >= Jp) continue;
             float P = 0.f, cnt = 0.f;
-            if (j < J) {
-                for (int l = 0; l < Lp && j + l < J; ++l) {
+#pragma unroll
+            for (int l = 0; l < M - p; ++l) {       // a source's taps are rows p .. p+L_n-1
+                if (l < Lp && j + l < J) {
                     P += sq[(p + l) * Jp + j + l];
                     cnt += 1.f;
                 }
