@@ -149,11 +149,11 @@ __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape 
     extern __shared__ float4 fsm4[];
     __shared__ float s_scale[CTFMNMF_MAX_M];
     __shared__ float red_cta[(kFrameThreads / 32) * CTFMNMF_MAX_M];
-    compute_scales(s, d, normalize, s_scale, red_cta);
-    if (blockIdx.x == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
     const Grp g{(int)threadIdx.x, kFrameThreads, 0};
-    if constexpr (BB <= 16) frame_item<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0);
-    else frame_item_wide<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0);
+    const ScaleJob job{s_scale, red_cta, normalize};     // formed while the item's staging is in flight
+    if constexpr (BB <= 16) frame_item<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+    else frame_item_wide<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+    if (blockIdx.x == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
 }
 
 static int frame_fc(const Shape& s, int BB)

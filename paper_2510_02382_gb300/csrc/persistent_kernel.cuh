@@ -149,13 +149,16 @@ persistent_kernel(const Shape s, const State d, const PersistArgs pa)
         alive = grid_sync(d, 2u * it + 1u, pa.timeout_ns, it == 0 && (int)blockIdx.x == pa.skip_cta);
         if (!alive) break;
         // ---- normalisation scale and frame items
-        compute_scales(s, d, pa.normalize, s_new, red_cta);
-        for (int item = blockIdx.x; item < items; item += gridDim.x)
-        {
+        // the first item of the CTA also forms the scale, overlapping its staging copies
+        const ScaleJob job{s_new, red_cta, pa.normalize};
+        bool scaled = false;
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
             // two frames per thread where the registers allow it (128 per thread here)
-            if constexpr (BB <= 10) frame_item<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0);
-            else frame_item_wide<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0);
+            if constexpr (BB <= 10) frame_item<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0, scaled ? nullptr : &job);
+            else frame_item_wide<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0, scaled ? nullptr : &job);
+            scaled = true;
         }
+        if (!scaled) compute_scales(s, d, pa.normalize, s_new, red_cta);
         alive = grid_sync(d, 2u * it + 2u, pa.timeout_ns, false);
         if (threadIdx.x < CTFMNMF_MAX_M) s_old[threadIdx.x] = s_new[threadIdx.x];
         __syncthreads();

@@ -52,7 +52,7 @@ __device__ __forceinline__ void reduce_scatter(float (&a)[V], int lane)
 // ---------------------------------------------------------------------------------------
 // Bin phase: shared memory of a group (floats), ragged sizes rounded so float4 views align
 struct BinSmem {
-    int ils, cw, sq, red, red2, total;   // offsets (floats)
+    int ils, cw, sq, red, red2, tpre, total;   // offsets (floats)
 };
 
 __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
@@ -64,7 +64,8 @@ __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
     b.sq = b.cw + N * Jp;                        // [M][Jp]
     b.red = b.sq + M * Jp;                       // [2][NW][32]   ISS partials
     b.red2 = b.red + 2 * NW * 32;                // [NW][N][2][32] basis-update partials
-    b.total = b.red2 + NW * N * 2 * 32 + 8;      // + row powers [NW][8] reuse red
+    b.tpre = b.red2 + NW * N * 2 * 32;           // [N * B] this bin's bases, prefetched
+    b.total = b.tpre + N * CTFMNMF_MAX_B;        // (row powers [NW][8] reuse red)
     b.total = (b.total + 3) & ~3;
     return b;
 }
@@ -94,6 +95,13 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
     float* sq = gsm + L.sq;
     float* red = gsm + L.red;
     float* red2 = gsm + L.red2;
+    float* tpre = gsm + L.tpre;
+
+    // ---- prefetch this bin's bases (used at the end; the load overlaps the staging)
+    for (int t = g.tid; t < N * B; t += g.nt) {
+        const int n = t / B, k = t - n * B;
+        tpre[t] = __ldcg(d.T + (size_t)n * s.FBp + (size_t)i * B + k);
+    }
 
     // ---- stage 1/lambda of this bin (cp.async, 16 bytes per copy; zero front pad)
     {
@@ -298,7 +306,7 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         }
         const float s0 = scale[s.row0[n]];
         float* Tp = d.T + (size_t)n * s.FBp + (size_t)i * B + k;
-        const float tcur = __ldcg(Tp) * (s0 * s0);
+        const float tcur = tpre[t] * (s0 * s0);
         const float tn = (den > 0.f) ? tcur * sqrtf(num / den) : tcur;
         __stcg(Tp, fmaxf(tn, kFloorNmf));
     }
@@ -405,6 +413,15 @@ __device__ __forceinline__ void stage_bases(const float* src, float* dst, int co
         cp_async16(reinterpret_cast<float4*>(dst) + e, reinterpret_cast<const float4*>(src) + e);
 }
 
+// The normalisation scale (compute_scales) to be formed inside the first frame item of a
+// CTA, after that item's staging copies are issued, so that the two round trips overlap.
+// Only valid when the item's group is the whole CTA.
+struct ScaleJob {
+    float* out;        // shared [M]
+    float* red_cta;    // shared scratch [(blockDim/32) * CTFMNMF_MAX_M]
+    int normalize;
+};
+
 // One frame-phase item (Eq. 18, all-taps form by default, then Eqs. 19-21 for the PSD):
 //   lambda'_{n,i,j} = sum_k T'[i][n][k] V[n][k][j],  T' = the bases of this iteration,
 //   num[k] = sum_i T'[i][n][k] P[i][n][j]/lambda'^2,  den[k] = sum_i T'[i][n][k] c_n(j)/lambda',
@@ -414,7 +431,8 @@ __device__ __forceinline__ void stage_bases(const float* src, float* dst, int co
 // the variant for many bases, BB = 32).
 template <int BB>
 __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, const int item, const Grp& g,
-                                           float* gsm, const int FC, const float* scale, const int v_tap0)
+                                           float* gsm, const int FC, const float* scale, const int v_tap0,
+                                           const ScaleJob* job = nullptr)
 {
     const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
     (void)M;
@@ -447,6 +465,7 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
             cp_async16(reinterpret_cast<float4*>(Ps) + e,
                        reinterpret_cast<const float4*>(d.P + ((size_t)(c0 + ii) * N + n) * Jp + j0) + h);
         }
+        if (job && c0 == 0) compute_scales(s, d, job->normalize, job->out, job->red_cta);
         cp_async_wait();
         grp_sync(g);
         if (valid) {
@@ -541,7 +560,8 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
 // and j0 + 2tx + 1, ty = tid >> 2 is the bin slice.
 template <int BB>
 __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
-                                           float* gsm, const int FC, const float* scale, const int v_tap0)
+                                           float* gsm, const int FC, const float* scale, const int v_tap0,
+                                           const ScaleJob* job = nullptr)
 {
     static_assert(BB % 2 == 0 && BB <= 16, "two-frame item needs an even BB <= 16");
     const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
@@ -581,6 +601,7 @@ __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const
             cp_async16(reinterpret_cast<float4*>(Ps) + e,
                        reinterpret_cast<const float4*>(d.P + ((size_t)(cb + ii) * N + n) * Jp + j0) + h);
         }
+        if (job && cb == 0) compute_scales(s, d, job->normalize, job->out, job->red_cta);
         cp_async_wait();
         grp_sync(g);
         for (int ii = ty; ii < nb; ii += NY) {
