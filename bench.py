@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--iters", type=int, default=None, help="iterations per step (default: workload's)")
+    p.add_argument("--batched-steps", type=int, default=3,
+                   help="timed steps of the 64-mixture batched workload (0 skips it)")
     return p.parse_args()
 
 
@@ -195,6 +197,42 @@ def run_reference(args):
     }))
 
 
+def batched_leg(args, peak):
+    """The ragged batched workload: 64 mixtures (J ~ U[300, 3000], N in {2, 3}, M = N + 1,
+    L in {2, 4, 8}, F = 513, B = 10, seeds 0..63), 50 iterations per step, one batch handle.
+    Its working set (about 3 GB) is far larger than L2, so no flush is needed."""
+    import torch
+    from paper_2510_02382_gb300 import synth
+    from paper_2510_02382_gb300.api import CTFMNMF, Batch
+    specs = synth.batched_specs()
+    solvers, bytes_it, binframes = [], 0, 0
+    for sp in specs:
+        mix = synth.make_mixture(sp)
+        sv = CTFMNMF(sp.M, sp.N, sp.L, sp.B, sp.F, sp.J, Ln=mix.Ln, path="two_kernel")
+        sv.load_stft(torch.from_numpy(mix.X).cuda())
+        sv.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+        solvers.append(sv)
+        bytes_it += 16 * sp.M * sp.F * sp.J + 8 * sp.N * sp.B * (sp.F + sp.J)
+        binframes += sp.F * sp.J
+    iters = specs[0].iters
+    batch = Batch(solvers)
+    batch.time(iters)
+    ms = [batch.time(iters) for _ in range(args.batched_steps)]
+    info = batch.info()
+    batch.close()
+    for sv in solvers:
+        sv.close()
+    t = statistics.median(ms) / 1000.0
+    achieved = bytes_it * iters / t / 1e9
+    return {"workload": "64 ragged mixtures: J ~ U[300, 3000], N in {2,3}, M = N+1, L in {2,4,8}, F=513, B=10, "
+                        "50 iterations per step, seeds 0..63",
+            "batch_iterations_per_s": iters / t, "bin_frames_per_s": binframes * iters / t,
+            "ms_per_step": 1000.0 * t, "steps": len(ms),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes_per_iteration": bytes_it},
+            "plan": info}
+
+
 def run_ours(args):
     import torch
     from paper_2510_02382_gb300 import synth
@@ -317,6 +355,7 @@ def run_ours(args):
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
     solver_path = solver.path
     solver.close()
+    batched = batched_leg(args, peak) if args.batched_steps > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -342,7 +381,10 @@ def run_ours(args):
                 "steps": e2e_steps},
         "clocks": clocks,
         "gpu_launches": launches,
+        "batched": batched,
     }
+    if batched is not None:
+        batched["vs_plain_bin_frames"] = batched["bin_frames_per_s"] / line["bin_frames_per_s"]
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

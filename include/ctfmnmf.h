@@ -195,6 +195,42 @@ int ctfmnmf_get_logdet(ctfmnmf_t h, double* logdet);
 /* NMF factors: device pointers, float32 T [N][F][B] and V [N][B][J]; either may be NULL. */
 int ctfmnmf_get_nmf(ctfmnmf_t h, float* T, float* V);
 
+/* ---- batched form: many mixtures advanced together ---- */
+
+typedef struct ctfmnmf_batch* ctfmnmf_batch_t;
+
+/*
+ * Group `count` solver handles (all created on the current device, with equal v_update
+ * and normalize options, each at most once) so that ctfmnmf_batch_iterate advances all of
+ * them with shared launches: per iteration one bin-phase launch per class of mixtures with
+ * equal template shape (M, frames per thread, block size), then one frame-phase launch per
+ * class of base counts; the launches of n iterations are captured once into a CUDA graph
+ * and replayed. The mixtures may differ in every dimension (ragged J, N, taps, B, F).
+ * The handles keep owning their state: load_stft, set_init, cost and get_* stay per
+ * handle; a handle must outlive the batch. The launch plan is chosen by an autotuner at
+ * creation (it times two iterations of each candidate plan on the handles' buffers, saving
+ * and restoring their state, so creating a batch changes no handle; it allocates and frees
+ * temporary device memory of about the size of the mixtures' state). Work runs on the
+ * stream of handles[0]. Errors: EINVAL, ENOMEM, EUNSUPPORTED (no plan fits), ECUDA;
+ * messages from ctfmnmf_last_error(NULL).
+ */
+int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* out);
+
+/* Run n_iter >= 0 iterations (as ctfmnmf_iterate) on every mixture of the batch;
+ * asynchronous. ESTATE if a mixture has no STFT loaded. */
+int ctfmnmf_batch_iterate(ctfmnmf_batch_t b, int n_iter);
+
+/* Diagnostic: ctfmnmf_batch_iterate(b, n_iter) between two CUDA events on the batch's
+ * stream; synchronises and writes the elapsed milliseconds to *ms (host). */
+int ctfmnmf_batch_time(ctfmnmf_batch_t b, int n_iter, double* ms);
+
+/* Diagnostic: info[5] (host) = {mixtures, bin classes, frame classes, chosen candidate
+ * plan (2 * eight-frames-preferred + merged-classes), kernels launched so far}. */
+int ctfmnmf_batch_info(ctfmnmf_batch_t b, int* info);
+
+/* Release the batch (not its handles). b may be NULL. */
+int ctfmnmf_batch_destroy(ctfmnmf_batch_t b);
+
 /*
  * ctfmnmf_cost_noalloc -- the negative log-likelihood of Eq. 5 (as ctfmnmf_cost) from
  * caller-held buffers, without allocating any device memory. The paper has no counterpart:

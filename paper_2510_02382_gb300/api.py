@@ -68,6 +68,11 @@ _SIGS = {
     "ctfmnmf_debug_skip_arrival": (c_int, [c_void_p, c_int]),
     "ctfmnmf_cost_noalloc": (c_int, [c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_batch_create": (c_int, [c_int, c_void_p, c_void_p]),
+    "ctfmnmf_batch_iterate": (c_int, [c_void_p, c_int]),
+    "ctfmnmf_batch_time": (c_int, [c_void_p, c_int, c_void_p]),
+    "ctfmnmf_batch_info": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_batch_destroy": (c_int, [c_void_p]),
 }
 
 
@@ -101,6 +106,42 @@ def _ptr(t) -> Optional[int]:
     if t is None:
         return None
     return t.data_ptr()
+
+
+class Batch:
+    """A ctfmnmf_batch_t over CTFMNMF solvers of one device: iterate() advances them all."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (c_void_p * len(self.solvers))(*[x._h.value for x in self.solvers])
+        h = c_void_p()
+        _check(lib().ctfmnmf_batch_create(len(self.solvers), arr, ctypes.byref(h)), None)
+        self._h = h
+
+    def iterate(self, n_iter: int):
+        _check(lib().ctfmnmf_batch_iterate(self._h, int(n_iter)), None)
+
+    def time(self, n_iter: int) -> float:
+        ms = c_double()
+        _check(lib().ctfmnmf_batch_time(self._h, int(n_iter), ctypes.byref(ms)), None)
+        return ms.value
+
+    def info(self):
+        out = (c_int * 5)()
+        _check(lib().ctfmnmf_batch_info(self._h, out), None)
+        keys = ("mixtures", "bin_classes", "frame_classes", "plan", "launches")
+        return dict(zip(keys, list(out)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ctfmnmf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cost_noalloc(Y, T, V, logdet, Ln, out, stream=None):

@@ -7,31 +7,7 @@
 
 #include <new>
 
-#include "internal.cuh"
-
-using ctf::Shape;
-using ctf::State;
-
-struct ctfmnmf {
-    Shape s;
-    State d;
-    ctfmnmf_options opt;
-    int L;
-    int device;
-    cudaStream_t stream;        // user stream (nullptr = legacy default stream)
-    cudaStream_t capture;       // private stream used to capture the iteration graph
-    bool loaded;
-    cudaGraphExec_t graph;
-    int graph_iters;
-    double* host_cost;          // pinned one-double landing buffer
-    float2* sepbuf;             // device images for ctfmnmf_get_separated_host (lazy)
-    long long launches;         // kernels enqueued so far
-    ctf::PersistPlan plan;      // persistent-path plan for this shape on this device
-    int path;                   // CTFMNMF_PATH_TWO_KERNEL or CTFMNMF_PATH_PERSISTENT
-    int skip_cta;               // test hook: block that skips its first barrier arrival
-    unsigned long long timeout_ns;
-    char err[256];
-};
+#include "handle.h"
 
 namespace {
 
@@ -83,9 +59,7 @@ int check_flag(ctfmnmf* h, int mask, const char* what)
     return CTFMNMF_OK;
 }
 
-// kernels per launcher: load 1, init_nmf 1, psd 1, bin/frame phase 1 each, finalize 2,
-// cost 2, separate 1, read-outs 1
-constexpr int kFinalizeKernels = 2;
+using ctf::kFinalizeKernels;
 
 // Synchronise the stream and report a device wait that ran out (then clear the report).
 int sync_and_check(ctfmnmf* h)
@@ -113,7 +87,12 @@ int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
     return CTFMNMF_OK;
 }
 
-long long iteration_kernels(int n_iter) { return 2LL * n_iter + kFinalizeKernels; }
+}  // namespace
+
+long long ctf::iteration_kernels(int n_iter) { return 2LL * n_iter + kFinalizeKernels; }
+
+namespace {
+using ctf::iteration_kernels;
 
 }  // namespace
 

@@ -56,6 +56,8 @@ size_t bin_phase_smem(const Shape& s)
     return sizeof(float) * (size_t)bin_smem_layout(s.M, s.N, s.Jp, nt).total;
 }
 
+int bin_smem_floats(const Shape& s, int nt) { return bin_smem_layout(s.M, s.N, s.Jp, nt).total; }
+
 template <int M, int FPT>
 static cudaError_t launch_mf(const Shape& s, const State& d, int v_tap0, int nt, cudaStream_t st,
                              bool configure_only)

@@ -1,0 +1,37 @@
+// The solver handle behind ctfmnmf_t (host side), shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+using ctf::Shape;
+using ctf::State;
+
+struct ctfmnmf {
+    Shape s;
+    State d;
+    ctfmnmf_options opt;
+    int L;
+    int device;
+    cudaStream_t stream;        // user stream (nullptr = legacy default stream)
+    cudaStream_t capture;       // private stream used to capture the iteration graph
+    bool loaded;
+    cudaGraphExec_t graph;
+    int graph_iters;
+    double* host_cost;          // pinned one-double landing buffer
+    float2* sepbuf;             // device images for ctfmnmf_get_separated_host (lazy)
+    long long launches;         // kernels enqueued so far
+    ctf::PersistPlan plan;      // persistent-path plan for this shape on this device
+    int path;                   // CTFMNMF_PATH_TWO_KERNEL or CTFMNMF_PATH_PERSISTENT
+    int skip_cta;               // test hook: block that skips its first barrier arrival
+    unsigned long long timeout_ns;
+    char err[256];
+};
+
+namespace ctf {
+// kernels enqueued by one ctfmnmf_iterate of n_iter iterations on the two-kernel path
+long long iteration_kernels(int n_iter);
+// finalize kernels (pending normalisation) launched at the end of every iterate call
+constexpr int kFinalizeKernels = 2;
+}  // namespace ctf

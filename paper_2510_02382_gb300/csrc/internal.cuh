@@ -88,12 +88,33 @@ cudaError_t launch_persistent(const Shape& s, const State& d, const PersistPlan&
                               int v_tap0, int normalize, unsigned long long timeout_ns, int skip_cta,
                               cudaStream_t st);
 
+// Batched path (batch.cu): one descriptor per mixture, launch classes of equal template
+// arguments; `work` lists the (mixture, bin) or (mixture, item) pair of every block.
+struct MixDesc {
+    Shape s;
+    State d;
+};
+struct BatchClass {
+    int M, fpt, nt, blocks;
+    size_t smem;
+    int2* work;        // device [blocks]
+};
+cudaError_t launch_batch_bin(const BatchClass& c, const MixDesc* mixes, int v_tap0, cudaStream_t st,
+                             bool configure);
+cudaError_t configure_batch_frame();
+int batch_frame_class(int B);
+int batch_frame_chunk(int B, int BB);
+cudaError_t launch_batch_frame(int BB, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
+                               int normalize, cudaStream_t st);
+
 // Set the message that ctfmnmf_last_error(NULL) returns on this thread.
 void set_thread_error(const char* msg);
 
 // Frames per thread / threads per block chosen for the bin phase; false if unsupported.
 bool bin_phase_config(int M, int J, int* fpt, int* threads);
 size_t bin_phase_smem(const Shape& s);
+// Shared floats of the bin phase for shape s with nt threads per block.
+int bin_smem_floats(const Shape& s, int nt);
 
 // ---------------------------------------------------------------- device helpers
 

@@ -1,0 +1,106 @@
+"""The batched form (ctfmnmf_batch_*) against the FP64 oracle and the single-mixture path."""
+import numpy as np
+import pytest
+
+from paper_2510_02382_gb300 import synth
+
+from gpu_helpers import cost_close, make_solver, rel_fro, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+RAGGED = [
+    # (M, N, Ln, F, J, B)
+    (3, 2, (2, 1), 9, 37, 4),
+    (4, 3, (2, 1, 1), 7, 611, 10),
+    (3, 2, (2, 1), 5, 1500, 10),
+    (2, 2, (1, 1), 11, 300, 3),
+    (6, 2, (3, 3), 4, 260, 16),
+    (4, 2, (2, 2), 3, 2900, 32),
+]
+
+
+def _loaded(mixes, **kw):
+    import torch
+    out = []
+    for mix in mixes:
+        s = make_solver(mix, path="two_kernel", **kw)
+        s.load_stft(torch.from_numpy(mix.X).cuda())
+        s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+        out.append(s)
+    return out
+
+
+def test_batch_of_ragged_mixtures_matches_oracle():
+    from paper_2510_02382_gb300.api import Batch
+    mixes = [synth.random_case(300 + k, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+             for k, (M, N, Ln, F, J, B) in enumerate(RAGGED)]
+    solvers = _loaded(mixes)
+    batch = Batch(solvers)
+    info = batch.info()
+    assert info["mixtures"] == len(mixes) and info["bin_classes"] >= 1
+    batch.iterate(1)
+    for s, mix in zip(solvers, mixes):
+        r = run_oracle(mix, 1)
+        assert rel_fro(s.get_demixed().cpu().numpy(), r["y"]) < 1e-4
+    batch.iterate(4)                     # 5 iterations in total
+    for s, mix in zip(solvers, mixes):
+        r = run_oracle(mix, 5)
+        sp = mix.spec
+        ok, err = cost_close(s.cost(), r["cost"], 1e-5, sp.F, sp.J, sp.M)
+        assert ok, (sp, err)
+        T, V = s.get_nmf()
+        assert rel_fro(V.cpu().numpy(), r["v"]) < 1e-3 and rel_fro(T.cpu().numpy(), r["b"]) < 1e-3
+    batch.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_creation_leaves_handles_unchanged_and_matches_single_path():
+    from paper_2510_02382_gb300.api import Batch
+    mixes = [synth.random_case(400 + k, M=3, N=2, F=6, J=J, B=4, Ln=(2, 1)) for k, J in enumerate((100, 700))]
+    solvers = _loaded(mixes)
+    before = [s.get_demixed().cpu().numpy() for s in solvers]
+    batch = Batch(solvers)
+    after = [s.get_demixed().cpu().numpy() for s in solvers]
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    batch.iterate(3)
+    ys = [s.get_demixed().cpu().numpy() for s in solvers]
+    single = _loaded(mixes)
+    for s, y in zip(single, ys):
+        s.iterate(3)
+        assert rel_fro(s.get_demixed().cpu().numpy(), y) < 1e-5
+        s.close()
+    batch.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_unloaded_member():
+    from paper_2510_02382_gb300.api import Batch, CtfMnmfError
+    mixes = [synth.random_case(500 + k, M=3, N=2, F=4, J=64, B=3, Ln=(2, 1)) for k in range(2)]
+    solvers = _loaded(mixes[:1]) + [make_solver(mixes[1], path="two_kernel")]
+    batch = Batch(solvers)
+    with pytest.raises(CtfMnmfError) as e:
+        batch.iterate(1)
+    assert e.value.name == "ESTATE"
+    batch.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batched_workload_sampled_mixtures():
+    """The 64-mixture ragged workload (J in [300, 3000], N in {2,3}, M = N+1, L in {2,4,8},
+    F = 513, B = 10): one batched iteration, three sampled mixtures checked against the oracle."""
+    from paper_2510_02382_gb300.api import Batch
+    specs = synth.batched_specs()
+    mixes = [synth.make_mixture(sp) for sp in specs]
+    solvers = _loaded(mixes)
+    batch = Batch(solvers)
+    batch.iterate(1)
+    for k in (0, 17, 63):
+        r = run_oracle(mixes[k], 1)
+        assert rel_fro(solvers[k].get_demixed().cpu().numpy(), r["y"]) < 1e-4, k
+    batch.close()
+    for s in solvers:
+        s.close()
