@@ -64,14 +64,19 @@ def workload_config(spec, l2_note):
 
 
 def csrc_hash():
-    """Short hash of the CUDA sources, matched against the one stored with a capture."""
+    """Short hash of the sources the persistent kernel is compiled from, matched against the
+    one stored with a capture."""
     import hashlib
     d = os.path.join(ROOT, "paper_2510_02382_gb300", "csrc")
+    names = sorted(f for f in os.listdir(d)
+                   if f in ("internal.cuh", "phases.cuh", "persistent_kernel.cuh") or f.startswith("persistent"))
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in names:
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "ctfmnmf.h"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -77,6 +77,8 @@ CONFIGS = {
     "P4": MixSpec("P4", N=2, M=4, L=2, tau=1.5, F=513, J=501, B=3, iters=100),
     "P6": MixSpec("P6", N=2, M=6, L=3, tau=2.0, F=513, J=501, B=3, iters=100),
     "P8": MixSpec("P8", N=2, M=8, L=4, tau=3.0, F=513, J=501, B=3, iters=100),
+    # differentiable workload: 20 unrolled iterations, a batch of 16 mixtures (seeds 0..15)
+    "C5": MixSpec("C5", N=2, M=3, L=4, tau=3.0, F=257, J=500, B=8, iters=20),
 }
 
 _TAU_BY_L = {2: 1.5, 4: 3.0, 8: 5.0}
@@ -97,6 +99,11 @@ def batched_specs(count: int = 64, F: int = 513, B: int = 10, iters: int = 50) -
         out.append(MixSpec(f"B{s}", N=N, M=N + 1, L=L, tau=_TAU_BY_L[L], F=F, J=J, B=B,
                            iters=iters, seed=s))
     return out
+
+
+def grad_specs(count: int = 16, **kw) -> List[MixSpec]:
+    """The differentiable batch: the C5 shape with seeds 0..count-1 (fields in ``kw`` replaced)."""
+    return [dataclasses.replace(CONFIGS["C5"], name=f"G{s}", seed=s, **kw) for s in range(count)]
 
 
 def scaled(spec: MixSpec, **kw) -> MixSpec:
