@@ -231,6 +231,61 @@ int ctfmnmf_batch_info(ctfmnmf_batch_t b, int* info);
 /* Release the batch (not its handles). b may be NULL. */
 int ctfmnmf_batch_destroy(ctfmnmf_batch_t b);
 
+/* ---- differentiable form: gradients through the unrolled iterations ---- */
+
+/*
+ * A ctfmnmf_grad_t runs n_iter unrolled iterations (as ctfmnmf_iterate, default options:
+ * all-taps activation update, normalisation) on a batch of S mixtures of one shape and
+ * back-propagates a gradient given on the separated images (Eq. 24 in its projection-back
+ * form, as ctfmnmf_get_separated) to the observations X and the initial factors T0, V0.
+ * The paper differentiates nothing: the backward pass is the adjoint of every forward step
+ * (ISS sweep Eqs. 11-16, basis MU Eq. 17, activation MU Eq. 18, normalisation Eqs. 19-21,
+ * images Eq. 24) in reverse order, written by hand.
+ * Gradient convention: for a real loss L and complex z = a + ib the gradient is
+ * dL/da + i dL/db (PyTorch's). At a floor (T, V or lambda clamped) the gradient through
+ * the clamped value is 0; a row with no energy (no normalisation) passes none through mu.
+ * Memory: the state (Y, W, T, V) of every mixture is copied every ckpt_every iterations
+ * during the forward pass (checkpoints); the backward pass recomputes one segment at a time
+ * from its checkpoint, keeping the state of every iteration of that segment.
+ * All device arguments are caller-owned; every call is asynchronous on the object's stream
+ * unless stated. Error messages: ctfmnmf_last_error(NULL) on the calling thread.
+ */
+typedef struct ctfmnmf_grad* ctfmnmf_grad_t;
+
+/* Create for `batch` >= 1 mixtures of shape dims with taps Ln[N] (NULL = derived from
+ * dims->L as ctfmnmf_create), n_iter >= 1 iterations, a checkpoint every ckpt_every >= 1
+ * iterations. EINVAL as ctfmnmf_create_ex; EUNSUPPORTED if M > 4, J > 2048 or B > 32;
+ * ENOMEM. Allocates every buffer the forward and backward passes use. */
+int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int n_iter, int ckpt_every,
+                        ctfmnmf_grad_t* out);
+
+/* All later work of g goes to this cudaStream_t (NULL = legacy default stream). */
+int ctfmnmf_grad_set_stream(ctfmnmf_grad_t g, void* stream);
+
+/* Forward pass: X [S][M][F][J] complex64, T0 [S][N][F][B], V0 [S][N][B][J] float32 (device,
+ * read; floored at 1e-12 as ctfmnmf_set_init), C [S][N][M][F][J] complex64 (device, written):
+ * the separated images after n_iter iterations from W = I. Inputs are not checked for NaN. */
+int ctfmnmf_grad_forward(ctfmnmf_grad_t g, const void* X, const float* T0, const float* V0, void* C);
+
+/* Backward pass of the last forward pass: gC [S][N][M][F][J] complex64 (device, read), the
+ * gradient of the loss with respect to C. Writes gX [S][M][F][J] complex64, gT0 [S][N][F][B]
+ * and gV0 [S][N][B][J] float32 (device). Each forward pass allows one backward pass (the
+ * backward pass recomputes over the forward state); ESTATE otherwise. */
+int ctfmnmf_grad_backward(ctfmnmf_grad_t g, const void* gC, void* gX, float* gT0, float* gV0);
+
+/* Loss head: the mean over all S*N*M*F*J elements of |C - Cref|^2 (C, Cref [S][N][M][F][J]
+ * complex64, device). If loss != NULL it is written to *loss (device double). If gC != NULL,
+ * gC = scale * d(loss)/dC is written (device complex64), scale = *dloss (device double) or 1
+ * when dloss is NULL. */
+int ctfmnmf_grad_mse(ctfmnmf_grad_t g, const void* C, const void* Cref, double* loss, const double* dloss,
+                     void* gC);
+
+/* Diagnostic: kernels g has enqueued so far (forward and backward passes), to *count (host). */
+int ctfmnmf_grad_launch_count(ctfmnmf_grad_t g, long long* count);
+
+/* Release g and its buffers (synchronises its stream). g may be NULL. */
+int ctfmnmf_grad_destroy(ctfmnmf_grad_t g);
+
 /*
  * ctfmnmf_cost_noalloc -- the negative log-likelihood of Eq. 5 (as ctfmnmf_cost) from
  * caller-held buffers, without allocating any device memory. The paper has no counterpart:

@@ -73,6 +73,13 @@ _SIGS = {
     "ctfmnmf_batch_time": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_batch_info": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_batch_destroy": (c_int, [c_void_p]),
+    "ctfmnmf_grad_create": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "ctfmnmf_grad_set_stream": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_grad_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_grad_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_grad_mse": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_grad_launch_count": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_grad_destroy": (c_int, [c_void_p]),
 }
 
 
@@ -135,6 +142,83 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().ctfmnmf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grad:
+    """A ctfmnmf_grad_t: n_iter unrolled iterations on a batch of S mixtures of one shape,
+    differentiable with respect to X [S][M][F][J] complex64, T0 [S][N][F][B] and
+    V0 [S][N][B][J] float32 through the separated images C [S][N][M][F][J] complex64
+    (checkpoint every ckpt_every iterations). See paper_2510_02382_gb300.autograd for the
+    torch.autograd.Function wrappers."""
+
+    def __init__(self, M: int, N: int, L: int, B: int, F: int, J: int, batch: int, n_iter: int,
+                 ckpt_every: int = 5, Ln: Optional[Sequence[int]] = None, stream=None):
+        import torch
+        self.M, self.N, self.L, self.B, self.F, self.J = M, N, L, B, F, J
+        self.S, self.n_iter, self.ckpt_every = batch, n_iter, ckpt_every
+        d = Dims(M, N, L, B, F, J)
+        ln_arr = (c_int * N)(*Ln) if Ln is not None else None
+        h = c_void_p()
+        _check(lib().ctfmnmf_grad_create(ctypes.byref(d), ln_arr, int(batch), int(n_iter), int(ckpt_every),
+                                         ctypes.byref(h)), None)
+        self._h = h
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().ctfmnmf_grad_set_stream(self._h, c_void_p(self.stream.cuda_stream)), None)
+
+    def shapes(self):
+        S, M, N, F, J, B = self.S, self.M, self.N, self.F, self.J, self.B
+        return {"X": (S, M, F, J), "T0": (S, N, F, B), "V0": (S, N, B, J), "C": (S, N, M, F, J)}
+
+    def forward(self, X, T0, V0, out=None):
+        import torch
+        sh = self.shapes()
+        CTFMNMF._expect(X, sh["X"], torch.complex64, cuda=True)
+        CTFMNMF._expect(T0, sh["T0"], torch.float32, cuda=True)
+        CTFMNMF._expect(V0, sh["V0"], torch.float32, cuda=True)
+        if out is None:
+            out = torch.empty(sh["C"], dtype=torch.complex64, device=X.device)
+        CTFMNMF._expect(out, sh["C"], torch.complex64, cuda=True)
+        _check(lib().ctfmnmf_grad_forward(self._h, c_void_p(X.data_ptr()), c_void_p(T0.data_ptr()),
+                                          c_void_p(V0.data_ptr()), c_void_p(out.data_ptr())), None)
+        return out
+
+    def backward(self, gC):
+        import torch
+        sh = self.shapes()
+        CTFMNMF._expect(gC, sh["C"], torch.complex64, cuda=True)
+        gX = torch.empty(sh["X"], dtype=torch.complex64, device=gC.device)
+        gT0 = torch.empty(sh["T0"], dtype=torch.float32, device=gC.device)
+        gV0 = torch.empty(sh["V0"], dtype=torch.float32, device=gC.device)
+        _check(lib().ctfmnmf_grad_backward(self._h, c_void_p(gC.data_ptr()), c_void_p(gX.data_ptr()),
+                                           c_void_p(gT0.data_ptr()), c_void_p(gV0.data_ptr())), None)
+        return gX, gT0, gV0
+
+    def mse(self, C, Cref, loss=None, dloss=None, gC=None):
+        """Loss head: loss (0-dim float64 device tensor) = mean |C - Cref|^2 and/or gC =
+        dloss * d(loss)/dC (dloss: 0-dim float64 device tensor, or None for 1)."""
+        import torch
+        sh = self.shapes()
+        CTFMNMF._expect(C, sh["C"], torch.complex64, cuda=True)
+        CTFMNMF._expect(Cref, sh["C"], torch.complex64, cuda=True)
+        _check(lib().ctfmnmf_grad_mse(self._h, c_void_p(C.data_ptr()), c_void_p(Cref.data_ptr()), _ptr(loss),
+                                      _ptr(dloss), _ptr(gC)), None)
+        return loss, gC
+
+    def launch_count(self) -> int:
+        out = ctypes.c_longlong()
+        _check(lib().ctfmnmf_grad_launch_count(self._h, ctypes.byref(out)), None)
+        return int(out.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ctfmnmf_grad_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -393,3 +393,12 @@ int ctfmnmf_batch_destroy(ctfmnmf_batch_t b)
 }
 
 }  // extern "C"
+
+namespace ctf {
+// The iterations of a batch enqueued on st as plain launches, without the finalize of the
+// pending normalisation (the differentiable form applies it itself and records it).
+cudaError_t batch_enqueue(ctfmnmf_batch_t b, int n_iter, cudaStream_t st)
+{
+    return enqueue_batch(b, b->plan, n_iter, st);
+}
+}  // namespace ctf

@@ -1,0 +1,1078 @@
+// Backward pass of unrolled CTF-MNMF-ISS: hand-written adjoint of one iteration (Sec. III)
+// and of the projection-back images (Eq. 24). Notation and buffers: grad.cuh.
+//
+// Per iteration t, in stream order:
+//   A grad_norm_kernel     (bin, mixture)          e_r = sum Re(conj(gY') Y') + Re(conj(gW') W')
+//                                                  + [l(r) = 0] 2 sum gT' T'   (the sigma sums)
+//   B grad_vmu_kernel      (128 frames, source, mixture)  denV by a sweep over all bins; from
+//                                                  dL/dV' the gradients of numV, denV and the
+//                                                  direct part V' = V R of dL/dV
+//   C grad_bin_kernel      (bin, mixture)          recompute the ISS sweep; adjoint of the
+//                                                  normalisation, the activation MU (per-bin
+//                                                  parts), the basis MU and the ISS sweep;
+//                                                  writes dL/dY, dL/dW, dL/dT of the bin and the
+//                                                  per-(bin, frame) terms kernel D needs
+//   D grad_vgather_kernel  (128 frames, source, mixture)  dL/dV += sum over bins of those terms
+#include <stdio.h>
+
+#include "grad.cuh"
+
+namespace ctf {
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Sum a[V] over the thread block; every thread finds the sums in out[V] (shared) afterwards.
+// red holds (threads / 32) * V floats.
+template <int V>
+__device__ __forceinline__ void block_sum(float (&a)[V], float* red, float* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int v = 0; v < V; ++v) a[v] = warp_sum(a[v]);
+    if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) red[warp * V + v] = a[v];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < V) {
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += red[w * V + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- A: normalisation sums
+template <int M>
+__global__ void __launch_bounds__(256) grad_norm_kernel(const Shape s, const StatePtrs* __restrict__ nxt_tab,
+                                                        const GradBufs g)
+{
+    __shared__ float red[8 * M];
+    __shared__ float out[M];
+    const int i = blockIdx.x, sm = blockIdx.y;
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    const StatePtrs nxt = nxt_tab[sm];
+    const float2* gYb = g.gY + ((size_t)sm * F + i) * M * Jp;
+    const float2* Yb = nxt.Y + (size_t)i * M * Jp;
+    float a[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        a[r] = 0.f;
+        for (int j = threadIdx.x; j < J; j += blockDim.x) {
+            const float2 gy = gYb[(size_t)r * Jp + j], y = Yb[(size_t)r * Jp + j];
+            a[r] = fmaf(gy.x, y.x, fmaf(gy.y, y.y, a[r]));
+        }
+    }
+    if ((int)threadIdx.x < M * M) {
+        const int p = threadIdx.x / M, c = threadIdx.x - p * M;
+        const float2 gw = g.gW[(((size_t)sm * F + i) * M + p) * M + c];
+        const float2 w = nxt.W[((size_t)i * M + p) * M + c];
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+            if (r == p) a[r] = fmaf(gw.x, w.x, fmaf(gw.y, w.y, a[r]));
+    }
+    for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
+        const int n = t / B, k = t - n * B;
+        const size_t o = (size_t)n * FBp + (size_t)i * B + k;
+        const float v = 2.f * g.gT[(size_t)sm * N * FBp + o] * nxt.T[o];
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+            if (r == s.row0[n]) a[r] += v;
+    }
+    block_sum<M>(a, red, out);
+    if ((int)threadIdx.x < M) atomicAdd(&g.e[sm * M + threadIdx.x], (double)out[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------- B: activation-MU gradients
+constexpr int kIC = 256;   // bins staged per pass
+
+template <int BB>
+__global__ void __launch_bounds__(kGradTile) grad_vmu_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
+                                                             const StatePtrs* __restrict__ nxt_tab, const GradBufs g,
+                                                             const int gin)
+{
+    __shared__ float T1s[kIC * BB];
+    const int sm = blockIdx.z, n = blockIdx.y, j = blockIdx.x * kGradTile + threadIdx.x;
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
+    const float s0 = g.sig[sm * s.M + s.row0[n]];
+    const float inv = 1.f / (s0 * s0);                 // T1 = T' / sigma_{(n,0)}^2
+    const bool live = j < J;
+    float v[BB], den[BB];
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        v[k] = (live && k < B) ? cur.V[((size_t)n * B + k) * Jp + j] : 0.f;
+        den[k] = 0.f;
+    }
+    const float c = live ? (float)min(s.Ln[n], J - j) : 0.f;   // taps l with j + l < J
+    for (int i0 = 0; i0 < F; i0 += kIC) {
+        const int ic = min(kIC, F - i0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < ic * BB; e += blockDim.x) {
+            const int ii = e / BB, k = e - ii * BB;
+            T1s[e] = k < B ? nxt.T[(size_t)n * FBp + (size_t)(i0 + ii) * B + k] * inv : 0.f;
+        }
+        __syncthreads();
+        if (live) {
+            for (int ii = 0; ii < ic; ++ii) {
+                const float* t1 = T1s + ii * BB;
+                float lam = 0.f;
+#pragma unroll
+                for (int k = 0; k < BB; ++k) lam = fmaf(t1[k], v[k], lam);
+                const float w = c / fmaxf(lam, kFloorPsd);
+#pragma unroll
+                for (int k = 0; k < BB; ++k) den[k] = fmaf(t1[k], w, den[k]);
+            }
+        }
+    }
+    if (j >= Jp) return;
+    const size_t base = ((size_t)sm * N + n) * B * (size_t)Jp + j;
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        if (k >= B) break;
+        const size_t idx = base + (size_t)k * Jp;
+        float gn = 0.f, gd = 0.f, gv = 0.f;
+        if (live) {
+            const float g1 = g.gV[gin][idx];
+            const float V1 = nxt.V[((size_t)n * B + k) * Jp + j], V = v[k];
+            if (V1 > kFloorNmf && V > 0.f && den[k] > 0.f) {
+                // V1 = V R, R = sqrt(numV / denV): dR/dnum = 1/(2 R den), dR/dden = -R/(2 den)
+                const float R = V1 / V, gR = g1 * V;
+                gn = gR / (2.f * R * den[k]);
+                gd = -gR * R / (2.f * den[k]);
+                gv = g1 * R;
+            }
+        }
+        g.gnum[idx] = gn;
+        g.gden[idx] = gd;
+        g.gV[1 - gin][idx] = gv;
+    }
+}
+
+// ---------------------------------------------------------------- C: per-bin adjoint
+template <int M, int FPT>
+__global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
+                                                       const StatePtrs* __restrict__ nxt_tab, const GradBufs g)
+{
+    constexpr int VF = 3 * M - 2;   // forward ISS sums per step: d_p, n_p (p != r), q
+    constexpr int VB = 2 * M - 1;   // backward ISS sums per step: G_p (p != r), Gs
+    constexpr int NB = kGradMaxM * CTFMNMF_MAX_B;
+    extern __shared__ float4 gsm4[];
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    float* invl = reinterpret_cast<float*>(gsm4);          // [N][Jp] 1/lambda (0 past J)
+    float* sq = invl + N * Jp;                             // [M][Jp] |Y1|^2
+    float* gS = sq + M * Jp;                               // [N][Jp] dL/d(delayed power)
+    float* gl = gS + N * Jp;                               // [N][Jp] dL/dlambda
+    float2* y0s = reinterpret_cast<float2*>(gl + N * Jp);  // [M][Jp] rows at the iteration start
+    __shared__ float2 Wv[M + 1][M][M];                     // W_i before step r of the sweep
+    __shared__ float2 zs[M][M];                            // z of step r
+    __shared__ float dsv[M][M];                            // d_p of step r (p != r), q at p = r
+    __shared__ float ssv[M];                               // q^{-1/2} of step r
+    __shared__ float2 gWs[M][M];                           // running dL/dW_i
+    __shared__ float Ti[NB], T1i[NB], gT1[NB], denT[NB], gnTs[NB], gdTs[NB], gTacc[NB];
+    __shared__ float red[16 * 16];
+    __shared__ float bout[16];
+    __shared__ float2 gn_b[M];
+    __shared__ float gd_b[M];
+    __shared__ float gq_b;
+
+    const int i = blockIdx.x, sm = blockIdx.y;
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
+    const float* sig = g.sig + sm * M;
+    const size_t tb = (size_t)sm * N * FBp;
+    const size_t fb = (size_t)sm * N;
+
+    // ---- bases of the bin, dL/dT1 = sigma_0^2 dL/dT', W_i, dL/dW1 = sigma dL/dW'
+    for (int t = tid; t < N * B; t += NT) {
+        const int n = t / B, k = t - n * B;
+        const size_t o = (size_t)n * FBp + (size_t)i * B + k;
+        const float s0 = sig[s.row0[n]];
+        Ti[t] = cur.T[o];
+        T1i[t] = nxt.T[o] / (s0 * s0);
+        gT1[t] = g.gT[tb + o] * (s0 * s0);
+        denT[t] = 0.f;
+        gTacc[t] = 0.f;
+    }
+    if (tid < M * M) {
+        const int p = tid / M, c = tid - p * M;
+        Wv[0][p][c] = cur.W[((size_t)i * M + p) * M + c];
+        const float2 gw = g.gW[(((size_t)sm * F + i) * M + p) * M + c];
+        gWs[p][c] = make_float2(gw.x * sig[p], gw.y * sig[p]);
+    }
+    __syncthreads();
+    // ---- 1/lambda of the iteration's T, V; the rows at the start of the iteration
+    for (int e = tid; e < N * Jp; e += NT) {
+        const int n = e / Jp, j = e - n * Jp;
+        float v = 0.f;
+        if (j < J) {
+            float lam = 0.f;
+            for (int k = 0; k < B; ++k) lam = fmaf(Ti[n * B + k], cur.V[((size_t)n * B + k) * Jp + j], lam);
+            v = 1.f / fmaxf(lam, kFloorPsd);
+        }
+        invl[e] = v;
+    }
+    {
+        const float2* Yc = cur.Y + (size_t)i * M * Jp;
+        for (int e = tid; e < M * Jp; e += NT) y0s[e] = Yc[e];
+    }
+    __syncthreads();
+
+    auto phi = [&](int p, int j) -> float {   // 1/lambda_{n(p), j - l(p)}, 0 when masked
+        const int l = s.row_l[p];
+        return (j >= l && j < J) ? invl[s.row_n[p] * Jp + j - l] : 0.f;
+    };
+
+    // ---- forward ISS sweep (Eqs. 11-16), keeping z, d, q of every step
+    float2 y[M][FPT];
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            y[r][f] = j < Jp ? y0s[r * Jp + j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        float a[VF];
+#pragma unroll
+        for (int v = 0; v < VF; ++v) a[v] = 0.f;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            const float2 yr = y[r][f];
+            const float yr2 = abs2(yr);
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const int q = p < r ? p : p - 1;
+                const float ph = phi(p, j);
+                const float2 c = cmul_conj(y[p][f], yr);
+                a[3 * q] = fmaf(ph, yr2, a[3 * q]);
+                a[3 * q + 1] = fmaf(ph, c.x, a[3 * q + 1]);
+                a[3 * q + 2] = fmaf(ph, c.y, a[3 * q + 2]);
+            }
+            a[VF - 1] = fmaf(phi(r, j), yr2, a[VF - 1]);
+        }
+        block_sum<VF>(a, red, bout);
+        if (tid == 0) {
+            float2 z[M];
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const int q = p < r ? p : p - 1;
+                const float d = bout[3 * q];
+                z[p] = d > 0.f ? make_float2(bout[3 * q + 1] / d, bout[3 * q + 2] / d) : make_float2(0.f, 0.f);
+                zs[r][p] = z[p];
+                dsv[r][p] = d;
+            }
+            const float qv = bout[VF - 1] / (float)J;
+            const float sr = qv > 0.f ? 1.f / sqrtf(qv) : 1.f;
+            z[r] = make_float2(1.f - sr, 0.f);
+            zs[r][r] = z[r];
+            dsv[r][r] = qv;
+            ssv[r] = sr;
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                const float2 wr = Wv[r][r][c];
+#pragma unroll
+                for (int p = 0; p < M; ++p) {
+                    const float2 w = Wv[r][p][c];
+                    if (p == r) Wv[r + 1][p][c] = make_float2(sr * wr.x, sr * wr.y);
+                    else {
+                        const float2 zw = cmulf(z[p], wr);
+                        Wv[r + 1][p][c] = make_float2(w.x - zw.x, w.y - zw.y);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const float2 yr = y[r][f];
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const float2 zy = cmulf(zs[r][p], yr);
+                y[p][f] = make_float2(y[p][f].x - zy.x, y[p][f].y - zy.y);
+            }
+            y[r][f] = make_float2(ssv[r] * yr.x, ssv[r] * yr.y);
+        }
+    }
+
+    // ---- normalisation adjoint: dL/dY1 = sigma (dL/dY' - (e_r / (F J)) Y'), Y' = sigma Y1
+    float2 gy[M][FPT];
+    {
+        const float2* gYb = g.gY + ((size_t)sm * F + i) * M * Jp;
+        const double FJ = (double)F * (double)J;
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            const float sg = sig[r];
+            const float coef = (float)(g.e[sm * M + r] / FJ);
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = tid + f * NT;
+                float2 v = make_float2(0.f, 0.f);
+                if (j < J) {
+                    const float2 gp = gYb[(size_t)r * Jp + j];
+                    v = make_float2(sg * (gp.x - coef * sg * y[r][f].x), sg * (gp.y - coef * sg * y[r][f].y));
+                }
+                gy[r][f] = v;
+                if (j < Jp) sq[r * Jp + j] = abs2(y[r][f]);
+            }
+        }
+    }
+    __syncthreads();
+
+    // delayed power S_n(j) = sum_{l < L_n, j + l < J} |Y1_{(n,l)}(j + l)|^2 and its tap count
+    auto delayed = [&](int n, int j, float* S, float* c) {
+        float acc = 0.f;
+        int cnt = 0;
+        const int r0 = s.row0[n], Lq = s.Ln[n];
+        for (int l = 0; l < Lq; ++l)
+            if (j + l < J) {
+                acc += sq[(r0 + l) * Jp + j + l];
+                ++cnt;
+            }
+        *S = acc;
+        *c = (float)cnt;
+    };
+
+    // ---- activation MU adjoint, this bin's part: numV = sum_i T1 A', denV = sum_i T1 c/lambda'
+    for (int n = 0; n < N; ++n) {
+        const float* Vn = cur.V + (size_t)n * B * Jp;
+        const float* gnum = g.gnum + (fb + n) * (size_t)B * Jp;
+        const float* gden = g.gden + (fb + n) * (size_t)B * Jp;
+        float Ap[FPT], cp[FPT], gp[FPT], ci[FPT];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            Ap[f] = cp[f] = gp[f] = ci[f] = 0.f;
+            if (j < J) {
+                float S, c;
+                delayed(n, j, &S, &c);
+                float raw = 0.f, gA = 0.f, gC = 0.f;
+                for (int k = 0; k < B; ++k) {
+                    const float t1 = T1i[n * B + k];
+                    raw = fmaf(t1, Vn[(size_t)k * Jp + j], raw);
+                    gA = fmaf(gnum[(size_t)k * Jp + j], t1, gA);
+                    gC = fmaf(gden[(size_t)k * Jp + j], t1, gC);
+                }
+                const float il = 1.f / fmaxf(raw, kFloorPsd);
+                const float A = S * il * il, cc = c * il;
+                Ap[f] = A;
+                cp[f] = cc;
+                gp[f] = raw > kFloorPsd ? (-2.f * A * il * gA - cc * il * gC) : 0.f;
+                gS[n * Jp + j] = gA * il * il;
+                ci[f] = c * invl[n * Jp + j];
+            }
+            if (j < Jp) g.glp[((fb + n) * F + i) * (size_t)Jp + j] = gp[f];
+        }
+        for (int k = 0; k < B; ++k) {
+            float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = tid + f * NT;
+                if (j < J) {
+                    const float vk = Vn[(size_t)k * Jp + j];
+                    a1 += gnum[(size_t)k * Jp + j] * Ap[f] + gden[(size_t)k * Jp + j] * cp[f] + gp[f] * vk;
+                    a2 = fmaf(vk, ci[f], a2);
+                }
+            }
+            a1 = warp_sum(a1);
+            a2 = warp_sum(a2);
+            if (lane == 0) {
+                atomicAdd(&gT1[n * B + k], a1);
+                atomicAdd(&denT[n * B + k], a2);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- basis MU adjoint (Eq. 17): T1 = T R, R = sqrt(numT / denT)
+    for (int t = tid; t < N * B; t += NT) {
+        const int n = t / B, k = t - n * B;
+        const float T = Ti[t], T1 = T1i[t], g1 = gT1[t], dn = denT[t];
+        float gTd = 0.f, gn = 0.f, gd = 0.f;
+        if (T1 > 1.0001f * kFloorNmf && T > 0.f && dn > 0.f) {
+            const float R = T1 / T, gR = g1 * T;
+            gTd = g1 * R;
+            gn = gR / (2.f * R * dn);
+            gd = -gR * R / (2.f * dn);
+        }
+        gTacc[t] = gTd;
+        gnTs[t] = gn;
+        gdTs[t] = gd;
+        const size_t o = tb + (size_t)n * FBp + (size_t)i * B + k;
+        g.gnT[o] = gn;
+        g.gdT[o] = gd;
+    }
+    __syncthreads();
+    for (int n = 0; n < N; ++n) {
+        const float* Vn = cur.V + (size_t)n * B * Jp;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            float A = 0.f;
+            if (j < J) {
+                float S, c;
+                delayed(n, j, &S, &c);
+                float raw = 0.f, gA = 0.f, gC = 0.f;
+                for (int k = 0; k < B; ++k) {
+                    const float vk = Vn[(size_t)k * Jp + j];
+                    raw = fmaf(Ti[n * B + k], vk, raw);
+                    gA = fmaf(gnTs[n * B + k], vk, gA);
+                    gC = fmaf(gdTs[n * B + k], vk, gC);
+                }
+                const float il = 1.f / fmaxf(raw, kFloorPsd);
+                A = S * il * il;
+                const float cc = c * il;
+                gS[n * Jp + j] += gA * il * il;
+                gl[n * Jp + j] = -2.f * A * il * gA - cc * il * gC;
+            } else if (j < Jp) {
+                gl[n * Jp + j] = 0.f;
+            }
+            if (j < Jp) g.aq[((fb + n) * F + i) * (size_t)Jp + j] = A;
+        }
+    }
+    __syncthreads();
+    // delayed power -> rows: dL/dY1_{(n,l)}(j) += 2 gS_n(j - l) Y1_{(n,l)}(j)
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        const int n = s.row_n[r], l = s.row_l[r];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            if (j >= l && j < J) {
+                const float w = 2.f * gS[n * Jp + j - l];
+                gy[r][f] = make_float2(gy[r][f].x + w * y[r][f].x, gy[r][f].y + w * y[r][f].y);
+            }
+        }
+    }
+
+    // ---- ISS sweep adjoint, steps r = M-1 .. 0
+    float gph[M][FPT];
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) gph[r][f] = 0.f;
+#pragma unroll
+    for (int r = M - 1; r >= 0; --r) {
+        // rows before step r: replay steps 0..r-1 from the iteration start with the stored z
+        float2 yw[M][FPT];
+#pragma unroll
+        for (int p = 0; p < M; ++p)
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = tid + f * NT;
+                yw[p][f] = j < Jp ? y0s[p * Jp + j] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int rr = 0; rr < r; ++rr)
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const float2 t = yw[rr][f];
+#pragma unroll
+                for (int p = 0; p < M; ++p) {
+                    if (p == rr) continue;
+                    const float2 zy = cmulf(zs[rr][p], t);
+                    yw[p][f] = make_float2(yw[p][f].x - zy.x, yw[p][f].y - zy.y);
+                }
+                yw[rr][f] = make_float2(ssv[rr] * t.x, ssv[rr] * t.y);
+            }
+        float a[VB];
+#pragma unroll
+        for (int v = 0; v < VB; ++v) a[v] = 0.f;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const float2 yr = yw[r][f];
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const int q = p < r ? p : p - 1;
+                const float2 c = cmul_conj(gy[p][f], yr);
+                a[2 * q] += c.x;
+                a[2 * q + 1] += c.y;
+            }
+            a[VB - 1] = fmaf(gy[r][f].x, yr.x, fmaf(gy[r][f].y, yr.y, a[VB - 1]));
+        }
+        block_sum<VB>(a, red, bout);
+        if (tid == 0) {
+            const float sr = ssv[r];
+            float gsv = bout[VB - 1];
+#pragma unroll
+            for (int c = 0; c < M; ++c) gsv = fmaf(gWs[r][c].x, Wv[r][r][c].x, fmaf(gWs[r][c].y, Wv[r][r][c].y, gsv));
+            float2 nw[M];
+#pragma unroll
+            for (int c = 0; c < M; ++c) nw[c] = make_float2(sr * gWs[r][c].x, sr * gWs[r][c].y);
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const int q = p < r ? p : p - 1;
+                float2 gz = make_float2(-bout[2 * q], -bout[2 * q + 1]);
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const float2 t = cmul_conj(gWs[p][c], Wv[r][r][c]);
+                    gz = make_float2(gz.x - t.x, gz.y - t.y);
+                    const float2 u = cmulf(conjf2(zs[r][p]), gWs[p][c]);
+                    nw[c] = make_float2(nw[c].x - u.x, nw[c].y - u.y);
+                }
+                const float d = dsv[r][p];
+                if (d > 0.f) {
+                    const float2 z = zs[r][p];
+                    gn_b[p] = make_float2(gz.x / d, gz.y / d);
+                    gd_b[p] = -(gz.x * z.x + gz.y * z.y) / d;
+                } else {
+                    gn_b[p] = make_float2(0.f, 0.f);
+                    gd_b[p] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < M; ++c) gWs[r][c] = nw[c];
+            gq_b = dsv[r][r] > 0.f ? -0.5f * sr * sr * sr * gsv : 0.f;
+        }
+        __syncthreads();
+        const float sr = ssv[r], gq = gq_b, invJ = 1.f / (float)J;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            if (j >= J) continue;
+            const float2 yr = yw[r][f];
+            const float yr2 = abs2(yr);
+            float2 ng = make_float2(sr * gy[r][f].x, sr * gy[r][f].y);
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const float ph = phi(p, j);
+                const float2 gn = gn_b[p];
+                const float gd = gd_b[p];
+                const float2 u = cmulf(conjf2(zs[r][p]), gy[p][f]);
+                const float2 w = cmulf(conjf2(gn), yw[p][f]);
+                ng = make_float2(ng.x - u.x + ph * w.x + 2.f * gd * ph * yr.x,
+                                 ng.y - u.y + ph * w.y + 2.f * gd * ph * yr.y);
+                const float2 t = cmul_conj(w, yr);       // conj(gn) y_p conj(y_r)
+                gph[p][f] += t.x + gd * yr2;
+            }
+            const float phr = phi(r, j);
+            ng = make_float2(ng.x + 2.f * invJ * gq * phr * yr.x, ng.y + 2.f * invJ * gq * phr * yr.y);
+            gph[r][f] += gq * invJ * yr2;
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                if (p == r) continue;
+                const float ph = phi(p, j);
+                const float2 t = cmulf(gn_b[p], yr);
+                gy[p][f] = make_float2(gy[p][f].x + ph * t.x, gy[p][f].y + ph * t.y);
+            }
+            gy[r][f] = ng;
+        }
+    }
+
+    // ---- outputs: dL/dY, dL/dW of the iteration start
+    {
+        float2* gYo = g.gY + ((size_t)sm * F + i) * M * Jp;
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = tid + f * NT;
+                if (j < Jp) gYo[(size_t)r * Jp + j] = j < J ? gy[r][f] : make_float2(0.f, 0.f);
+            }
+        if (tid < M * M) {
+            const int p = tid / M, c = tid - p * M;
+            g.gW[(((size_t)sm * F + i) * M + p) * M + c] = gWs[p][c];
+        }
+    }
+    // ISS part of dL/dlambda: phi_r(j) = 1/lambda_{n, j-l} => dL/dlambda -= dL/dphi phi^2.
+    // For one tap l every (n, j - l) target belongs to one thread.
+    int lmax = 0;
+    for (int n = 0; n < N; ++n) lmax = max(lmax, s.Ln[n]);
+    for (int l = 0; l < lmax; ++l) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            if (s.row_l[r] != l) continue;
+            const int n = s.row_n[r];
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = tid + f * NT;
+                if (j >= l && j < J) {
+                    const float ph = invl[n * Jp + j - l];
+                    gl[n * Jp + j - l] -= gph[r][f] * ph * ph;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---- lambda = T V: dL/dT += sum_j dL/dlambda V (this bin); the V part goes to kernel D
+    for (int n = 0; n < N; ++n) {
+        const float* Vn = cur.V + (size_t)n * B * Jp;
+        float gv[FPT];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = tid + f * NT;
+            float v = 0.f;
+            if (j < J) {
+                float raw = 0.f;
+                for (int k = 0; k < B; ++k) raw = fmaf(Ti[n * B + k], Vn[(size_t)k * Jp + j], raw);
+                v = raw > kFloorPsd ? gl[n * Jp + j] : 0.f;
+            }
+            gv[f] = v;
+            if (j < Jp) g.glt[((fb + n) * F + i) * (size_t)Jp + j] = v;
+        }
+        for (int k = 0; k < B; ++k) {
+            float a = 0.f;
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = tid + f * NT;
+                if (j < J) a = fmaf(gv[f], Vn[(size_t)k * Jp + j], a);
+            }
+            a = warp_sum(a);
+            if (lane == 0) atomicAdd(&gTacc[n * B + k], a);
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < N * B; t += NT) {
+        const int n = t / B, k = t - n * B;
+        g.gT[tb + (size_t)n * FBp + (size_t)i * B + k] = gTacc[t];
+    }
+}
+
+// ---------------------------------------------------------------- D: gather dL/dV over bins
+constexpr int kID = 64;    // bins staged per pass
+
+template <int BB>
+__global__ void __launch_bounds__(kGradTile) grad_vgather_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
+                                                                 const StatePtrs* __restrict__ nxt_tab,
+                                                                 const GradBufs g, const int gout)
+{
+    __shared__ float T1s[kID * BB], Ts[kID * BB], gns[kID * BB], gds[kID * BB];
+    const int sm = blockIdx.z, n = blockIdx.y, j = blockIdx.x * kGradTile + threadIdx.x;
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
+    const float s0 = g.sig[sm * s.M + s.row0[n]];
+    const float inv = 1.f / (s0 * s0);
+    const bool live = j < J;
+    const size_t tb = (size_t)sm * N * FBp + (size_t)n * FBp;
+    const size_t rows = ((size_t)sm * N + n) * F;
+    float v[BB], acc[BB];
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        v[k] = (live && k < B) ? cur.V[((size_t)n * B + k) * Jp + j] : 0.f;
+        acc[k] = 0.f;
+    }
+    const float c = live ? (float)min(s.Ln[n], J - j) : 0.f;
+    for (int i0 = 0; i0 < F; i0 += kID) {
+        const int ic = min(kID, F - i0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < ic * BB; e += blockDim.x) {
+            const int ii = e / BB, k = e - ii * BB;
+            const size_t o = (size_t)(i0 + ii) * B + k;
+            const bool ok = k < B;
+            T1s[e] = ok ? nxt.T[(size_t)n * FBp + o] * inv : 0.f;
+            Ts[e] = ok ? cur.T[(size_t)n * FBp + o] : 0.f;
+            gns[e] = ok ? g.gnT[tb + o] : 0.f;
+            gds[e] = ok ? g.gdT[tb + o] : 0.f;
+        }
+        __syncthreads();
+        if (live) {
+            for (int ii = 0; ii < ic; ++ii) {
+                const size_t q = (rows + i0 + ii) * (size_t)Jp + j;
+                const float glp = g.glp[q], glt = g.glt[q], A = g.aq[q];
+                const float* t = Ts + ii * BB;
+                float lam = 0.f;
+#pragma unroll
+                for (int k = 0; k < BB; ++k) lam = fmaf(t[k], v[k], lam);
+                const float ci = c / fmaxf(lam, kFloorPsd);
+                const float* t1 = T1s + ii * BB;
+                const float* gn = gns + ii * BB;
+                const float* gd = gds + ii * BB;
+#pragma unroll
+                for (int k = 0; k < BB; ++k)
+                    acc[k] = fmaf(glp, t1[k], fmaf(glt, t[k], fmaf(gn[k], A, fmaf(gd[k], ci, acc[k]))));
+            }
+        }
+    }
+    if (!live) return;
+    const size_t base = ((size_t)sm * N + n) * B * (size_t)Jp + j;
+#pragma unroll
+    for (int k = 0; k < BB; ++k)
+        if (k < B) g.gV[gout][base + (size_t)k * Jp] += acc[k];
+}
+
+// ---------------------------------------------------------------- images (Eq. 24) adjoint
+// c_n = sum_{r in n} H[:, r] y_r with H = W^{-1}: dL/dy_r = H[:, r]^H dL/dc_{n(r)},
+// dL/dH = sum_j dL/dc y^H, dL/dW = -H^H (dL/dH) H^H.
+template <int M>
+__global__ void __launch_bounds__(256) grad_head_kernel(const Shape s, const StatePtrs* __restrict__ live_tab,
+                                                        const float2* __restrict__ gC, const GradBufs g)
+{
+    constexpr int V = 2 * M * M;
+    __shared__ double a[M][2 * M][2];
+    __shared__ float2 H[M][M];
+    __shared__ float red[8 * V];
+    __shared__ float out[V];
+    const int i = blockIdx.x, sm = blockIdx.y;
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    const StatePtrs lv = live_tab[sm];
+    if (threadIdx.x == 0) {
+        // Gauss-Jordan elimination with partial pivoting on [W | I] in FP64
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < 2 * M; ++q) {
+                if (q < M) {
+                    const float2 w = lv.W[((size_t)i * M + p) * M + q];
+                    a[p][q][0] = w.x;
+                    a[p][q][1] = w.y;
+                } else {
+                    a[p][q][0] = (q - M == p) ? 1.0 : 0.0;
+                    a[p][q][1] = 0.0;
+                }
+            }
+        for (int c = 0; c < M; ++c) {
+            int piv = c;
+            double best = -1.0;
+            for (int p = c; p < M; ++p) {
+                const double m2 = a[p][c][0] * a[p][c][0] + a[p][c][1] * a[p][c][1];
+                if (m2 > best) {
+                    best = m2;
+                    piv = p;
+                }
+            }
+            if (piv != c)
+                for (int q = 0; q < 2 * M; ++q)
+                    for (int t = 0; t < 2; ++t) {
+                        const double x = a[c][q][t];
+                        a[c][q][t] = a[piv][q][t];
+                        a[piv][q][t] = x;
+                    }
+            const double pr = a[c][c][0], pi = a[c][c][1], den = pr * pr + pi * pi;
+            const double ir = pr / den, ii = -pi / den;
+            for (int q = 0; q < 2 * M; ++q) {
+                const double xr = a[c][q][0], xi = a[c][q][1];
+                a[c][q][0] = xr * ir - xi * ii;
+                a[c][q][1] = xr * ii + xi * ir;
+            }
+            for (int p = 0; p < M; ++p) {
+                if (p == c) continue;
+                const double fr = a[p][c][0], fi = a[p][c][1];
+                for (int q = 0; q < 2 * M; ++q) {
+                    const double xr = a[c][q][0], xi = a[c][q][1];
+                    a[p][q][0] -= fr * xr - fi * xi;
+                    a[p][q][1] -= fr * xi + fi * xr;
+                }
+            }
+        }
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < M; ++q) H[p][q] = make_float2((float)a[p][M + q][0], (float)a[p][M + q][1]);
+    }
+    __syncthreads();
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    const float2* Yb = lv.Y + (size_t)i * M * Jp;
+    float2* gYo = g.gY + ((size_t)sm * F + i) * M * Jp;
+    for (int j = threadIdx.x; j < Jp; j += blockDim.x) {
+        float2 gyv[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) gyv[r] = make_float2(0.f, 0.f);
+        if (j < J) {
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                const float2 yr = Yb[(size_t)r * Jp + j];
+                const int n = s.row_n[r];
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const float2 gc = gC[((((size_t)sm * N + n) * M + m) * F + i) * J + j];
+                    const float2 u = cmulf(conjf2(H[m][r]), gc);
+                    gyv[r] = make_float2(gyv[r].x + u.x, gyv[r].y + u.y);
+                    const float2 w = cmul_conj(gc, yr);
+                    acc[2 * (m * M + r)] += w.x;
+                    acc[2 * (m * M + r) + 1] += w.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < M; ++r) gYo[(size_t)r * Jp + j] = gyv[r];
+    }
+    block_sum<V>(acc, red, out);
+    if (threadIdx.x == 0) {
+        float2 gH[M][M], P[M][M];
+        for (int m = 0; m < M; ++m)
+            for (int r = 0; r < M; ++r) gH[m][r] = make_float2(out[2 * (m * M + r)], out[2 * (m * M + r) + 1]);
+        for (int m = 0; m < M; ++m)          // P = gH H^H
+            for (int c = 0; c < M; ++c) {
+                float2 t = make_float2(0.f, 0.f);
+                for (int r = 0; r < M; ++r) {
+                    const float2 u = cmul_conj(gH[m][r], H[c][r]);
+                    t = make_float2(t.x + u.x, t.y + u.y);
+                }
+                P[m][c] = t;
+            }
+        for (int p = 0; p < M; ++p)          // dL/dW = -H^H P
+            for (int c = 0; c < M; ++c) {
+                float2 t = make_float2(0.f, 0.f);
+                for (int m = 0; m < M; ++m) {
+                    const float2 u = cmulf(conjf2(H[m][p]), P[m][c]);
+                    t = make_float2(t.x + u.x, t.y + u.y);
+                }
+                g.gW[(((size_t)sm * F + i) * M + p) * M + c] = make_float2(-t.x, -t.y);
+            }
+    }
+    for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
+        const int n = t / B, k = t - n * B;
+        g.gT[(size_t)sm * N * FBp + (size_t)n * FBp + (size_t)i * B + k] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------- inputs
+// Y_0 = X (W_0 = I): dL/dX[m][i][j] = dL/dY_0[i][m][j]; T, V were floored on entry, so the
+// gradient passes where the stored initial value is above the floor.
+__global__ void grad_inputs_kernel(const Shape s, const StatePtrs* __restrict__ init_tab, const GradBufs g,
+                                   float2* __restrict__ gX, float* __restrict__ gT0)
+{
+    const int i = blockIdx.x, m = blockIdx.y, sm = blockIdx.z;
+    const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    const float2* src = g.gY + (((size_t)sm * F + i) * M + m) * Jp;
+    float2* dst = gX + (((size_t)sm * M + m) * F + i) * J;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) dst[j] = src[j];
+    if (m == 0) {
+        const StatePtrs in = init_tab[sm];
+        for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
+            const int n = t / B, k = t - n * B;
+            const size_t o = (size_t)n * FBp + (size_t)i * B + k;
+            gT0[(((size_t)sm * N + n) * F + i) * B + k] = in.T[o] > kFloorNmf ? g.gT[(size_t)sm * N * FBp + o] : 0.f;
+        }
+    }
+}
+
+__global__ void grad_v0_kernel(const Shape s, const StatePtrs* __restrict__ init_tab, const float* __restrict__ gV,
+                               float* __restrict__ gV0)
+{
+    const int row = blockIdx.x, sm = blockIdx.y;     // row = n * B + k
+    const int N = s.N, B = s.B, J = s.J, Jp = s.Jp;
+    const float* vin = init_tab[sm].V + (size_t)row * Jp;
+    const float* src = gV + ((size_t)sm * N * B + row) * Jp;
+    float* dst = gV0 + ((size_t)sm * N * B + row) * J;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) dst[j] = vin[j] > kFloorNmf ? src[j] : 0.f;
+}
+
+// ---------------------------------------------------------------- state copies (checkpoints)
+__global__ void grad_copy_kernel(const Shape s, const StatePtrs* __restrict__ src_tab,
+                                 const StatePtrs* __restrict__ dst_tab)
+{
+    const int sm = blockIdx.y;
+    const StatePtrs a = src_tab[sm], b = dst_tab[sm];
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nY = (size_t)s.F * s.M * s.Jp / 2;            // float4 = two complex values
+    const size_t nW = (size_t)s.F * s.M * s.M;
+    const size_t nT = (size_t)s.N * s.FBp / 4;
+    const size_t nV = (size_t)s.N * s.B * s.Jp / 4;
+    for (size_t e = t0; e < nY; e += stride) reinterpret_cast<float4*>(b.Y)[e] = reinterpret_cast<const float4*>(a.Y)[e];
+    for (size_t e = t0; e < nW; e += stride) b.W[e] = a.W[e];
+    for (size_t e = t0; e < nT; e += stride) reinterpret_cast<float4*>(b.T)[e] = reinterpret_cast<const float4*>(a.T)[e];
+    for (size_t e = t0; e < nV; e += stride) reinterpret_cast<float4*>(b.V)[e] = reinterpret_cast<const float4*>(a.V)[e];
+}
+
+// ---------------------------------------------------------------- finalize with sigma record
+// As finalize_kernel (the pending normalisation applied to Y, W, log|det|, T) for every
+// mixture of the batch; also records sigma_r = the applied scale.
+__global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* __restrict__ sig)
+{
+    const int i = blockIdx.x, r = blockIdx.y, sm = blockIdx.z;
+    const Shape& s = mixes[sm].s;
+    const State& d = mixes[sm].d;
+    const int M = s.M, B = s.B, Jp = s.Jp;
+    if (i >= s.F || r >= M) return;
+    const float sc = d.scale[r];
+    float2* row = d.Y + ((size_t)i * M + r) * Jp;
+    for (int j = threadIdx.x; j < Jp; j += blockDim.x) {
+        const float2 v = row[j];
+        row[j] = make_float2(v.x * sc, v.y * sc);
+    }
+    if ((int)threadIdx.x < M) {
+        float2* w = d.W + ((size_t)i * M + r) * M + threadIdx.x;
+        *w = make_float2(w->x * sc, w->y * sc);
+    }
+    if (r == 0 && threadIdx.x == 0) {
+        double f = d.ldm[i];
+        for (int p = 0; p < M; ++p) f *= (double)d.scale[p];
+        d.logdet[i] += log(f) + (double)d.lde[i] * 0.69314718055994530942;
+        d.ldm[i] = 1.0;
+        d.lde[i] = 0;
+    }
+    if (s.row_l[r] == 0 && (int)threadIdx.x < B) d.T[(size_t)s.row_n[r] * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
+    if (i == 0 && threadIdx.x == 0) sig[sm * M + r] = sc;
+}
+
+__global__ void grad_reset_scale_kernel(const MixDesc* __restrict__ mixes)
+{
+    const MixDesc& md = mixes[blockIdx.x];
+    if ((int)threadIdx.x < md.s.M) md.d.scale[threadIdx.x] = 1.f;
+}
+
+// ---------------------------------------------------------------- MSE loss head
+__global__ void __launch_bounds__(256) grad_mse_kernel(const size_t count, const float2* __restrict__ C,
+                                                       const float2* __restrict__ R, double* __restrict__ loss,
+                                                       const double* __restrict__ dloss, float2* __restrict__ gC)
+{
+    __shared__ double part[8];
+    const double inv = 1.0 / (double)count;
+    const float gs = gC ? (float)(2.0 * (dloss ? *dloss : 1.0) * inv) : 0.f;
+    double acc = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const float2 c = C[e], r = R[e];
+        const float2 d = make_float2(c.x - r.x, c.y - r.y);
+        acc += (double)(d.x * d.x + d.y * d.y);
+        if (gC) gC[e] = make_float2(gs * d.x, gs * d.y);
+    }
+    if (!loss) return;
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(loss, t * inv);
+    }
+}
+
+// ---------------------------------------------------------------- host launchers
+namespace {
+
+int pick_fpt(int Jp, int* nt)
+{
+    for (int fpt = 1; fpt <= 4; fpt *= 2) {
+        const int t = ((Jp + fpt - 1) / fpt + 31) / 32 * 32;
+        if (t <= 512) {
+            *nt = t < 64 ? 64 : t;
+            return fpt;
+        }
+    }
+    return 0;
+}
+
+size_t bin_smem(const Shape& s) { return sizeof(float) * (size_t)(3 * s.N + 3 * s.M) * s.Jp; }
+
+int pick_bb(int B) { return B <= 4 ? 4 : B <= 8 ? 8 : B <= 16 ? 16 : 32; }
+
+template <int M, int FPT>
+cudaError_t bin_mf(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt, const GradBufs& g, int nt,
+                   cudaStream_t st, bool configure)
+{
+    const size_t smem = bin_smem(s);
+    if (configure) return cudaFuncSetAttribute(grad_bin_kernel<M, FPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    grad_bin_kernel<M, FPT><<<dim3(s.F, S), nt, smem, st>>>(s, cur, nxt, g);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t bin_m(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt, const GradBufs& g,
+                  cudaStream_t st, bool configure)
+{
+    int nt = 0;
+    switch (pick_fpt(s.Jp, &nt)) {
+        case 1: return bin_mf<M, 1>(s, S, cur, nxt, g, nt, st, configure);
+        case 2: return bin_mf<M, 2>(s, S, cur, nxt, g, nt, st, configure);
+        case 4: return bin_mf<M, 4>(s, S, cur, nxt, g, nt, st, configure);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bin(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt, const GradBufs& g,
+                       cudaStream_t st, bool configure)
+{
+    switch (s.M) {
+        case 2: return bin_m<2>(s, S, cur, nxt, g, st, configure);
+        case 3: return bin_m<3>(s, S, cur, nxt, g, st, configure);
+        case 4: return bin_m<4>(s, S, cur, nxt, g, st, configure);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t grad_configure(const Shape& s)
+{
+    GradBufs g;
+    memset(&g, 0, sizeof(g));
+    return launch_bin(s, 1, nullptr, nullptr, g, nullptr, true);
+}
+
+cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt,
+                                   const GradBufs& g, int gin, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(g.e, 0, sizeof(double) * S * s.M, st);
+    if (e != cudaSuccess) return e;
+    switch (s.M) {
+        case 2: grad_norm_kernel<2><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
+        case 3: grad_norm_kernel<3><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
+        case 4: grad_norm_kernel<4><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
+        default: return cudaErrorInvalidValue;
+    }
+    const dim3 fgrid((s.Jp + kGradTile - 1) / kGradTile, s.N, S);
+    switch (pick_bb(s.B)) {
+        case 4: grad_vmu_kernel<4><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
+        case 8: grad_vmu_kernel<8><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
+        case 16: grad_vmu_kernel<16><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
+        default: grad_vmu_kernel<32><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
+    }
+    e = launch_bin(s, S, cur, nxt, g, st, false);
+    if (e != cudaSuccess) return e;
+    switch (pick_bb(s.B)) {
+        case 4: grad_vgather_kernel<4><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        case 8: grad_vgather_kernel<8><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        case 16: grad_vgather_kernel<16><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        default: grad_vgather_kernel<32><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t grad_launch_head(const Shape& s, int S, const StatePtrs* live, const float2* gC, const GradBufs& g,
+                             cudaStream_t st)
+{
+    switch (s.M) {
+        case 2: grad_head_kernel<2><<<dim3(s.F, S), 256, 0, st>>>(s, live, gC, g); break;
+        case 3: grad_head_kernel<3><<<dim3(s.F, S), 256, 0, st>>>(s, live, gC, g); break;
+        case 4: grad_head_kernel<4><<<dim3(s.F, S), 256, 0, st>>>(s, live, gC, g); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t grad_launch_inputs(const Shape& s, int S, const StatePtrs* init, const GradBufs& g, int gcur,
+                               float2* gX, float* gT0, float* gV0, cudaStream_t st)
+{
+    grad_inputs_kernel<<<dim3(s.F, s.M, S), 256, 0, st>>>(s, init, g, gX, gT0);
+    grad_v0_kernel<<<dim3(s.N * s.B, S), 256, 0, st>>>(s, init, g.gV[gcur], gV0);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_launch_copy(const Shape& s, int S, const StatePtrs* src, const StatePtrs* dst, cudaStream_t st)
+{
+    grad_copy_kernel<<<dim3(64, S), 256, 0, st>>>(s, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, float* sig, cudaStream_t st)
+{
+    grad_finalize_kernel<<<dim3(s.F, s.M, S), 256, 0, st>>>(mixes, sig);
+    grad_reset_scale_kernel<<<S, 32, 0, st>>>(mixes);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_launch_mse(size_t count, const float2* C, const float2* Cref, double* loss, const double* dloss,
+                            float2* gC, cudaStream_t st)
+{
+    if (loss) {
+        const cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), st);
+        if (e != cudaSuccess) return e;
+    }
+    grad_mse_kernel<<<1024, 256, 0, st>>>(count, C, Cref, loss, dloss, gC);
+    return cudaGetLastError();
+}
+
+}  // namespace ctf

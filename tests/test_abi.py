@@ -101,3 +101,25 @@ def test_default_factor_generator_reference_values():
     out = synth.splitmix64(np.array([0, 0x9E3779B97F4A7C15], dtype=np.uint64))
     assert int(out[0]) == 0xE220A8397B1DCDAF
     assert int(out[1]) == 0x6E789E6AA1B965F4
+
+
+def test_grad_form_rejects_bad_arguments_on_host(lib):
+    h = ctypes.c_void_p(123)
+    d = api.Dims(3, 2, 2, 8, 9, 32)
+    assert lib.ctfmnmf_grad_create(None, None, 2, 20, 5, ctypes.byref(h)) == -1
+    assert lib.ctfmnmf_grad_create(ctypes.byref(d), None, 0, 20, 5, ctypes.byref(h)) == -1
+    assert lib.ctfmnmf_grad_create(ctypes.byref(d), None, 2, 0, 5, ctypes.byref(h)) == -1
+    assert lib.ctfmnmf_grad_create(ctypes.byref(d), None, 2, 20, 0, ctypes.byref(h)) == -1
+    assert h.value is None
+    assert lib.ctfmnmf_grad_create(ctypes.byref(api.Dims(5, 2, 3, 8, 9, 32)), None, 2, 20, 5,
+                                   ctypes.byref(h)) == -7      # M > 4
+    assert "M <= 4" in lib.ctfmnmf_last_error(None).decode()
+    assert lib.ctfmnmf_grad_create(ctypes.byref(api.Dims(3, 2, 2, 8, 9, 3000)), None, 2, 20, 5,
+                                   ctypes.byref(h)) == -7      # J > 2048
+    out = ctypes.c_longlong()
+    assert lib.ctfmnmf_grad_forward(None, None, None, None, None) == -1
+    assert lib.ctfmnmf_grad_backward(None, None, None, None, None) == -1
+    assert lib.ctfmnmf_grad_mse(None, None, None, None, None, None) == -1
+    assert lib.ctfmnmf_grad_launch_count(None, ctypes.byref(out)) == -1
+    assert lib.ctfmnmf_grad_set_stream(None, None) == -1
+    assert lib.ctfmnmf_grad_destroy(None) == 0
