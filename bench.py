@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--iters", type=int, default=None, help="iterations per step (default: workload's)")
     p.add_argument("--batched-steps", type=int, default=3,
                    help="timed steps of the 64-mixture batched workload (0 skips it)")
+    p.add_argument("--fwdbwd-steps", type=int, default=3,
+                   help="timed steps of the 16-mixture forward + backward workload (0 skips it)")
     return p.parse_args()
 
 
@@ -75,8 +77,6 @@ def csrc_hash():
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(ROOT, "include", "ctfmnmf.h"), "rb") as fh:
-        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -238,6 +238,71 @@ def batched_leg(args, peak):
             "plan": info}
 
 
+def fwd_bwd_leg(args, peak):
+    """The differentiable workload: 16 mixtures (N=2, M=3, L=4, F=257, J=500, B=8, seeds
+    0..15), 20 unrolled iterations with a checkpoint every 5; a step = forward pass, MSE loss
+    and its gradient, backward pass to X, T0, V0 (all in the library's kernels). Timed with
+    CUDA events on the solver's stream; the forward pass alone (with the loss) is timed
+    beside it for the fwd+bwd / fwd cost ratio."""
+    import torch
+    from paper_2510_02382_gb300 import synth
+    from paper_2510_02382_gb300.api import Grad
+    specs = synth.grad_specs()
+    sp = specs[0]
+    S, K = len(specs), sp.iters
+    mixes = [synth.make_mixture(x) for x in specs]
+    g = Grad(sp.M, sp.N, sp.L, sp.B, sp.F, sp.J, batch=S, n_iter=K, ckpt_every=5, Ln=mixes[0].Ln)
+    X = torch.from_numpy(np.stack([m.X for m in mixes])).cuda()
+    T0 = torch.from_numpy(np.stack([m.T0 for m in mixes])).cuda()
+    V0 = torch.from_numpy(np.stack([m.V0 for m in mixes])).cuda()
+    Cref = torch.from_numpy(np.stack([m.images for m in mixes])).cuda()
+    C = torch.empty(g.shapes()["C"], dtype=torch.complex64, device="cuda")
+    gC = torch.empty_like(C)
+    loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    st = g.stream
+
+    def fwd():
+        g.forward(X, T0, V0, out=C)
+        g.mse(C, Cref, loss=loss)
+
+    def fwd_bwd():
+        fwd()
+        g.mse(C, Cref, gC=gC)
+        return g.backward(gC)
+
+    def timed(fn, n):
+        out = []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    fwd_bwd()                                   # first call builds the batch (autotuner)
+    timed(fwd_bwd, 1)
+    l0 = g.launch_count()
+    ms = timed(fwd_bwd, args.fwdbwd_steps)
+    launches = (g.launch_count() - l0) // args.fwdbwd_steps
+    ms_fwd = timed(fwd, args.fwdbwd_steps)
+    g.close()
+    t = ms / 1000.0
+    y_pass = 8 * sp.M * sp.F * sp.J * S         # one read or write of Y for the whole batch
+    bytes_it = 6 * y_pass                       # fwd+bwd counted as 6 Y-passes per iteration
+    achieved = bytes_it * K / t / 1e9
+    return {"workload": f"16 mixtures N={sp.N} M={sp.M} L={sp.L} F={sp.F} J={sp.J} B={sp.B}, {K} unrolled "
+                        "iterations, checkpoint every 5, loss = MSE of the separated images to the true "
+                        "images, gradients to X, T0, V0; seeds 0..15",
+            "iterations_per_s": K / t, "bin_frames_per_s": S * sp.F * sp.J * K / t,
+            "ms_per_step": ms, "fwd_ms_per_step": ms_fwd, "fwd_bwd_over_fwd": ms / ms_fwd,
+            "steps": args.fwdbwd_steps, "gpu_launches_per_step": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes_per_iteration": bytes_it}}
+
+
 def run_ours(args):
     import torch
     from paper_2510_02382_gb300 import synth
@@ -361,6 +426,7 @@ def run_ours(args):
     solver_path = solver.path
     solver.close()
     batched = batched_leg(args, peak) if args.batched_steps > 0 else None
+    fwdbwd = fwd_bwd_leg(args, peak) if args.fwdbwd_steps > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -387,9 +453,12 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": launches,
         "batched": batched,
+        "fwd_bwd": fwdbwd,
     }
     if batched is not None:
         batched["vs_plain_bin_frames"] = batched["bin_frames_per_s"] / line["bin_frames_per_s"]
+    if fwdbwd is not None:
+        fwdbwd["vs_plain_bin_frames"] = fwdbwd["bin_frames_per_s"] / line["bin_frames_per_s"]
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
