@@ -12,10 +12,12 @@
 //                                                  parts), the basis MU and the ISS sweep;
 //                                                  writes dL/dY, dL/dW, dL/dT of the bin and the
 //                                                  per-(bin, frame) terms kernel D needs
-//   D grad_vgather_kernel  (128 frames, source, mixture)  dL/dV += sum over bins of those terms
+//   D grad_vgather_kernel  (128 frames x 32 bins, source, mixture)  dL/dV += sum over those
+//                                                  bins of those terms (float atomics)
 #include <stdio.h>
 
 #include "grad.cuh"
+#include "phases.cuh"
 
 namespace ctf {
 
@@ -153,9 +155,11 @@ __global__ void __launch_bounds__(kGradTile) grad_vmu_kernel(const Shape s, cons
 }
 
 // ---------------------------------------------------------------- C: per-bin adjoint
+// Threads per block: up to 256 for FPT <= 2 (three blocks per SM), up to 512 for FPT = 4.
 template <int M, int FPT>
-__global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
-                                                       const StatePtrs* __restrict__ nxt_tab, const GradBufs g)
+__global__ void __launch_bounds__(FPT == 4 ? 512 : 256, FPT == 4 ? 1 : 3)
+grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const StatePtrs* __restrict__ nxt_tab,
+                const GradBufs g, const int vstage)
 {
     constexpr int VF = 3 * M - 2;   // forward ISS sums per step: d_p, n_p (p != r), q
     constexpr int VB = 2 * M - 1;   // backward ISS sums per step: G_p (p != r), Gs
@@ -167,6 +171,7 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
     float* gS = sq + M * Jp;                               // [N][Jp] dL/d(delayed power)
     float* gl = gS + N * Jp;                               // [N][Jp] dL/dlambda
     float2* y0s = reinterpret_cast<float2*>(gl + N * Jp);  // [M][Jp] rows at the iteration start
+    float* Vst = reinterpret_cast<float*>(y0s + M * Jp);   // [N][B][Jp] V, when vstage
     __shared__ float2 Wv[M + 1][M][M];                     // W_i before step r of the sweep
     __shared__ float2 zs[M][M];                            // z of step r
     __shared__ float dsv[M][M];                            // d_p of step r (p != r), q at p = r
@@ -218,8 +223,13 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
     {
         const float2* Yc = cur.Y + (size_t)i * M * Jp;
         for (int e = tid; e < M * Jp; e += NT) y0s[e] = Yc[e];
+        if (vstage)
+            for (int e = tid; e < N * B * Jp / 4; e += NT)
+                reinterpret_cast<float4*>(Vst)[e] = reinterpret_cast<const float4*>(cur.V)[e];
     }
     __syncthreads();
+    const float* Vsrc = vstage ? Vst : cur.V;              // V [N][B][Jp], shared or global
+    const float thr = 1.f / kFloorPsd;                     // 1/lambda at (or past) the floor
 
     auto phi = [&](int p, int j) -> float {   // 1/lambda_{n(p), j - l(p)}, 0 when masked
         const int l = s.row_l[p];
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
 
     // ---- activation MU adjoint, this bin's part: numV = sum_i T1 A', denV = sum_i T1 c/lambda'
     for (int n = 0; n < N; ++n) {
-        const float* Vn = cur.V + (size_t)n * B * Jp;
+        const float* Vn = Vsrc + (size_t)n * B * Jp;
         const float* gnum = g.gnum + (fb + n) * (size_t)B * Jp;
         const float* gden = g.gden + (fb + n) * (size_t)B * Jp;
         float Ap[FPT], cp[FPT], gp[FPT], ci[FPT];
@@ -371,22 +381,31 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
             }
             if (j < Jp) g.glp[((fb + n) * F + i) * (size_t)Jp + j] = gp[f];
         }
-        for (int k = 0; k < B; ++k) {
-            float a1 = 0.f, a2 = 0.f;
+        // per-bin sums over frames, 8 bases at a time: a[kk] -> dL/dT1, a[8 + kk] -> denT
+        for (int kb = 0; kb < B; kb += 8) {
+            float a[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) a[v] = 0.f;
 #pragma unroll
             for (int f = 0; f < FPT; ++f) {
                 const int j = tid + f * NT;
                 if (j < J) {
-                    const float vk = Vn[(size_t)k * Jp + j];
-                    a1 += gnum[(size_t)k * Jp + j] * Ap[f] + gden[(size_t)k * Jp + j] * cp[f] + gp[f] * vk;
-                    a2 = fmaf(vk, ci[f], a2);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const int k = kb + kk;
+                        if (k < B) {
+                            const size_t o = (size_t)k * Jp + j;
+                            const float vk = Vn[o];
+                            a[kk] += gnum[o] * Ap[f] + gden[o] * cp[f] + gp[f] * vk;
+                            a[8 + kk] = fmaf(vk, ci[f], a[8 + kk]);
+                        }
+                    }
                 }
             }
-            a1 = warp_sum(a1);
-            a2 = warp_sum(a2);
-            if (lane == 0) {
-                atomicAdd(&gT1[n * B + k], a1);
-                atomicAdd(&denT[n * B + k], a2);
+            reduce_scatter<16>(a, lane);
+            if (!(lane & 1)) {
+                const int v = lane >> 1, k = kb + (v & 7);
+                if (k < B) atomicAdd(v < 8 ? &gT1[n * B + k] : &denT[n * B + k], a[0]);
             }
         }
     }
@@ -412,7 +431,7 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
     }
     __syncthreads();
     for (int n = 0; n < N; ++n) {
-        const float* Vn = cur.V + (size_t)n * B * Jp;
+        const float* Vn = Vsrc + (size_t)n * B * Jp;
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const int j = tid + f * NT;
@@ -420,14 +439,13 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
             if (j < J) {
                 float S, c;
                 delayed(n, j, &S, &c);
-                float raw = 0.f, gA = 0.f, gC = 0.f;
+                float gA = 0.f, gC = 0.f;
                 for (int k = 0; k < B; ++k) {
                     const float vk = Vn[(size_t)k * Jp + j];
-                    raw = fmaf(Ti[n * B + k], vk, raw);
                     gA = fmaf(gnTs[n * B + k], vk, gA);
                     gC = fmaf(gdTs[n * B + k], vk, gC);
                 }
-                const float il = 1.f / fmaxf(raw, kFloorPsd);
+                const float il = invl[n * Jp + j];
                 A = S * il * il;
                 const float cc = c * il;
                 gS[n * Jp + j] += gA * il * il;
@@ -608,29 +626,31 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
     __syncthreads();
     // ---- lambda = T V: dL/dT += sum_j dL/dlambda V (this bin); the V part goes to kernel D
     for (int n = 0; n < N; ++n) {
-        const float* Vn = cur.V + (size_t)n * B * Jp;
+        const float* Vn = Vsrc + (size_t)n * B * Jp;
         float gv[FPT];
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const int j = tid + f * NT;
             float v = 0.f;
-            if (j < J) {
-                float raw = 0.f;
-                for (int k = 0; k < B; ++k) raw = fmaf(Ti[n * B + k], Vn[(size_t)k * Jp + j], raw);
-                v = raw > kFloorPsd ? gl[n * Jp + j] : 0.f;
-            }
+            if (j < J) v = invl[n * Jp + j] < thr ? gl[n * Jp + j] : 0.f;   // 0 where lambda is floored
             gv[f] = v;
             if (j < Jp) g.glt[((fb + n) * F + i) * (size_t)Jp + j] = v;
         }
-        for (int k = 0; k < B; ++k) {
-            float a = 0.f;
+        for (int kb = 0; kb < B; kb += 8) {
+            float a[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) a[v] = 0.f;
 #pragma unroll
             for (int f = 0; f < FPT; ++f) {
                 const int j = tid + f * NT;
-                if (j < J) a = fmaf(gv[f], Vn[(size_t)k * Jp + j], a);
+                if (j < J) {
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        if (kb + kk < B) a[kk] = fmaf(gv[f], Vn[(size_t)(kb + kk) * Jp + j], a[kk]);
+                }
             }
-            a = warp_sum(a);
-            if (lane == 0) atomicAdd(&gTacc[n * B + k], a);
+            reduce_scatter<8>(a, lane);
+            if (!(lane & 3) && kb + (lane >> 2) < B) atomicAdd(&gTacc[n * B + kb + (lane >> 2)], a[0]);
         }
     }
     __syncthreads();
@@ -641,7 +661,7 @@ __global__ void __launch_bounds__(512) grad_bin_kernel(const Shape s, const Stat
 }
 
 // ---------------------------------------------------------------- D: gather dL/dV over bins
-constexpr int kID = 64;    // bins staged per pass
+constexpr int kID = 32;    // bins per block (blocks of one frame tile add into dL/dV)
 
 template <int BB>
 __global__ void __launch_bounds__(kGradTile) grad_vgather_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
@@ -649,8 +669,9 @@ __global__ void __launch_bounds__(kGradTile) grad_vgather_kernel(const Shape s, 
                                                                  const GradBufs g, const int gout)
 {
     __shared__ float T1s[kID * BB], Ts[kID * BB], gns[kID * BB], gds[kID * BB];
-    const int sm = blockIdx.z, n = blockIdx.y, j = blockIdx.x * kGradTile + threadIdx.x;
     const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
+    const int tiles = (Jp + kGradTile - 1) / kGradTile;
+    const int sm = blockIdx.z, n = blockIdx.y, j = (blockIdx.x % tiles) * kGradTile + threadIdx.x;
     const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
     const float s0 = g.sig[sm * s.M + s.row0[n]];
     const float inv = 1.f / (s0 * s0);
@@ -664,9 +685,9 @@ __global__ void __launch_bounds__(kGradTile) grad_vgather_kernel(const Shape s, 
         acc[k] = 0.f;
     }
     const float c = live ? (float)min(s.Ln[n], J - j) : 0.f;
-    for (int i0 = 0; i0 < F; i0 += kID) {
+    {
+        const int i0 = blockIdx.x / tiles * kID;          // this block's bins [i0, i0 + ic)
         const int ic = min(kID, F - i0);
-        __syncthreads();
         for (int e = threadIdx.x; e < ic * BB; e += blockDim.x) {
             const int ii = e / BB, k = e - ii * BB;
             const size_t o = (size_t)(i0 + ii) * B + k;
@@ -678,6 +699,7 @@ __global__ void __launch_bounds__(kGradTile) grad_vgather_kernel(const Shape s, 
         }
         __syncthreads();
         if (live) {
+#pragma unroll 4
             for (int ii = 0; ii < ic; ++ii) {
                 const size_t q = (rows + i0 + ii) * (size_t)Jp + j;
                 const float glp = g.glp[q], glt = g.glt[q], A = g.aq[q];
@@ -699,7 +721,7 @@ __global__ void __launch_bounds__(kGradTile) grad_vgather_kernel(const Shape s, 
     const size_t base = ((size_t)sm * N + n) * B * (size_t)Jp + j;
 #pragma unroll
     for (int k = 0; k < BB; ++k)
-        if (k < B) g.gV[gout][base + (size_t)k * Jp] += acc[k];
+        if (k < B) atomicAdd(&g.gV[gout][base + (size_t)k * Jp], acc[k]);
 }
 
 // ---------------------------------------------------------------- images (Eq. 24) adjoint
@@ -942,19 +964,29 @@ __global__ void __launch_bounds__(256) grad_mse_kernel(const size_t count, const
 // ---------------------------------------------------------------- host launchers
 namespace {
 
+// Frames per thread of the per-bin adjoint: the fewest that keep the block at <= 256
+// threads (cheaper block reductions, more independent loads per thread), else 4 frames
+// with up to 512 threads.
 int pick_fpt(int Jp, int* nt)
 {
-    for (int fpt = 1; fpt <= 4; fpt *= 2) {
-        const int t = ((Jp + fpt - 1) / fpt + 31) / 32 * 32;
-        if (t <= 512) {
-            *nt = t < 64 ? 64 : t;
-            return fpt;
+    for (int lim = 256; lim <= 512; lim += 256)
+        for (int fpt = 1; fpt <= 4; fpt *= 2) {
+            const int t = ((Jp + fpt - 1) / fpt + 31) / 32 * 32;
+            if (t <= lim) {
+                *nt = t < 64 ? 64 : t;
+                return fpt;
+            }
         }
-    }
     return 0;
 }
 
-size_t bin_smem(const Shape& s) { return sizeof(float) * (size_t)(3 * s.N + 3 * s.M) * s.Jp; }
+size_t bin_smem(const Shape& s, bool vstage)
+{
+    return sizeof(float) * (size_t)(3 * s.N + 3 * s.M + (vstage ? s.N * s.B : 0)) * s.Jp;
+}
+
+// Stage V in shared memory when the block then still fits three to an SM.
+bool stage_v(const Shape& s) { return bin_smem(s, true) <= 64 * 1024; }
 
 int pick_bb(int B) { return B <= 4 ? 4 : B <= 8 ? 8 : B <= 16 ? 16 : 32; }
 
@@ -962,10 +994,11 @@ template <int M, int FPT>
 cudaError_t bin_mf(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt, const GradBufs& g, int nt,
                    cudaStream_t st, bool configure)
 {
-    const size_t smem = bin_smem(s);
+    const bool vs = stage_v(s);
+    const size_t smem = bin_smem(s, vs);
     if (configure) return cudaFuncSetAttribute(grad_bin_kernel<M, FPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
-    grad_bin_kernel<M, FPT><<<dim3(s.F, S), nt, smem, st>>>(s, cur, nxt, g);
+    grad_bin_kernel<M, FPT><<<dim3(s.F, S), nt, smem, st>>>(s, cur, nxt, g, vs ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1022,11 +1055,12 @@ cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, 
     }
     e = launch_bin(s, S, cur, nxt, g, st, false);
     if (e != cudaSuccess) return e;
+    const dim3 dgrid(fgrid.x * ((s.F + kID - 1) / kID), s.N, S);
     switch (pick_bb(s.B)) {
-        case 4: grad_vgather_kernel<4><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
-        case 8: grad_vgather_kernel<8><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
-        case 16: grad_vgather_kernel<16><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
-        default: grad_vgather_kernel<32><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        case 4: grad_vgather_kernel<4><<<dgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        case 8: grad_vgather_kernel<8><<<dgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        case 16: grad_vgather_kernel<16><<<dgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
+        default: grad_vgather_kernel<32><<<dgrid, kGradTile, 0, st>>>(s, cur, nxt, g, 1 - gin); break;
     }
     return cudaGetLastError();
 }
