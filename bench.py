@@ -50,6 +50,8 @@ def parse():
                    help="timed steps of the 64-mixture batched workload (0 skips it)")
     p.add_argument("--fwdbwd-steps", type=int, default=3,
                    help="timed steps of the 16-mixture forward + backward workload (0 skips it)")
+    p.add_argument("--ip-steps", type=int, default=3,
+                   help="timed steps of the ISS-vs-IP comparison on the plain workload (0 skips it)")
     return p.parse_args()
 
 
@@ -303,6 +305,43 @@ def fwd_bwd_leg(args, peak):
                          "frac": achieved / peak, "algorithmic_bytes_per_iteration": bytes_it}}
 
 
+def ip_leg(args, spec, iters):
+    """The paper's comparison on one GPU: the plain workload's iterations with the IP update
+    (Eqs. 9-10) against the ISS update, both on the two-kernel path (the IP update runs
+    there only), CUDA events around ctfmnmf_iterate on the solver's stream, median of the
+    timed steps, L2 flushed between steps. The persistent ISS path is the headline value."""
+    import torch
+    from paper_2510_02382_gb300 import synth
+    from paper_2510_02382_gb300.api import CTFMNMF
+    mix = synth.make_mixture(spec)
+    X = torch.from_numpy(mix.X).cuda()
+    T0 = torch.from_numpy(mix.T0).cuda()
+    V0 = torch.from_numpy(mix.V0).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {}
+    for upd in ("iss", "ip"):
+        sv = CTFMNMF(spec.M, spec.N, spec.L, spec.B, spec.F, spec.J, Ln=mix.Ln, path="two_kernel", w_update=upd)
+        st = sv.stream
+        ms = []
+        for k in range(args.ip_steps + 1):
+            sv.load_stft(X)
+            sv.set_init(T0, V0)
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sv.iterate(iters)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if k > 0:
+                ms.append(e0.elapsed_time(e1))
+        sv.close()
+        out[upd] = iters / (statistics.median(ms) / 1000.0)
+    return {"workload": "the plain workload, two-kernel path, ISS and IP updates", "steps": args.ip_steps,
+            "iss_iterations_per_s": out["iss"], "ip_iterations_per_s": out["ip"],
+            "iss_over_ip": out["iss"] / out["ip"]}
+
+
 def run_ours(args):
     import torch
     from paper_2510_02382_gb300 import synth
@@ -427,6 +466,7 @@ def run_ours(args):
     solver.close()
     batched = batched_leg(args, peak) if args.batched_steps > 0 else None
     fwdbwd = fwd_bwd_leg(args, peak) if args.fwdbwd_steps > 0 else None
+    ipcmp = ip_leg(args, spec, iters) if args.ip_steps > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -454,6 +494,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "batched": batched,
         "fwd_bwd": fwdbwd,
+        "iss_vs_ip": ipcmp,
     }
     if batched is not None:
         batched["vs_plain_bin_frames"] = batched["bin_frames_per_s"] / line["bin_frames_per_s"]

@@ -74,8 +74,18 @@ typedef struct ctfmnmf_options {
                                   0 (default) = 2000 ms. A wait that runs out ends the
                                   launch and the next ctfmnmf_synchronize (or any call that
                                   synchronises) returns CTFMNMF_ETIMEOUT                 */
-    int reserved[3];           /* must be zero                                          */
+    int w_update;              /* CTFMNMF_W_ISS (default): the ISS sweep of Eqs. 11-16;
+                                  CTFMNMF_W_IP: the IP update of Eqs. 9-10 that ISS
+                                  replaces (M <= 4, two-kernel path only, not in a batch;
+                                  keeps a copy of X, 8*M*F*J more bytes)                */
+    int reserved[2];           /* must be zero                                          */
 } ctfmnmf_options;
+
+/* Demixing updates (ctfmnmf_options.w_update). */
+enum {
+    CTFMNMF_W_ISS = 0,
+    CTFMNMF_W_IP = 1
+};
 
 /* Execution paths of ctfmnmf_iterate. PERSISTENT: all iterations of a call in one
  * cooperative launch with a grid-wide barrier between the per-bin and the cross-bin

@@ -18,6 +18,7 @@ c_int, c_void_p, c_double, c_char_p = ctypes.c_int, ctypes.c_void_p, ctypes.c_do
 STATUS = {0: "OK", -1: "EINVAL", -2: "ESTATE", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
           -6: "ENOMEM", -7: "EUNSUPPORTED"}
 V_ALL_TAPS, V_TAP0 = 0, 1
+W_ISS, W_IP = 0, 1
 
 
 class Dims(ctypes.Structure):
@@ -26,7 +27,7 @@ class Dims(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("v_update", c_int), ("normalize", c_int), ("use_graph", c_int), ("path", c_int),
-                ("wait_timeout_ms", c_int), ("reserved", c_int * 3)]
+                ("wait_timeout_ms", c_int), ("w_update", c_int), ("reserved", c_int * 2)]
 
 
 PATHS = {"auto": 0, "two_kernel": 1, "persistent": 2}
@@ -254,7 +255,7 @@ class CTFMNMF:
     def __init__(self, M: int, N: int, L: int, B: int, F: int, J: int,
                  Ln: Optional[Sequence[int]] = None, v_update: str = "all_taps",
                  normalize: bool = True, use_graph: bool = True, path: str = "auto",
-                 wait_timeout_ms: int = 0, stream=None):
+                 wait_timeout_ms: int = 0, w_update: str = "iss", stream=None):
         import torch
         self.M, self.N, self.L, self.B, self.F, self.J = M, N, L, B, F, J
         d = Dims(M, N, L, B, F, J)
@@ -265,6 +266,7 @@ class CTFMNMF:
         o.use_graph = int(bool(use_graph))
         o.path = PATHS[path]
         o.wait_timeout_ms = int(wait_timeout_ms)
+        o.w_update = {"iss": W_ISS, "ip": W_IP}[w_update]
         ln_arr = (c_int * N)(*Ln) if Ln is not None else None
         h = c_void_p()
         rc = lib().ctfmnmf_create_ex(ctypes.byref(d), ln_arr, ctypes.byref(o), ctypes.byref(h))

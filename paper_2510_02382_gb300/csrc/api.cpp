@@ -33,7 +33,7 @@ void free_state(ctfmnmf* h)
 {
     State& d = h->d;
     void* ptrs[] = {d.Y, d.W, d.logdet, d.T, d.V, d.invlam, d.P, d.mupart, d.scale, d.flag,
-                    d.cost_part, d.cost_out, d.staging, d.ldm, d.lde, d.sync};
+                    d.cost_part, d.cost_out, d.staging, d.ldm, d.lde, d.sync, d.X};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     memset(&h->d, 0, sizeof(h->d));
@@ -79,8 +79,9 @@ int sync_and_check(ctfmnmf* h)
 int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
 {
     const int tap0 = h->opt.v_update == CTFMNMF_V_TAP0;
+    const bool ip = h->opt.w_update == CTFMNMF_W_IP;
     for (int t = 0; t < n_iter; ++t) {
-        CUDA_TRY(h, ctf::launch_bin_phase(h->s, h->d, tap0, st));
+        CUDA_TRY(h, ip ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, st) : ctf::launch_bin_phase(h->s, h->d, tap0, st));
         CUDA_TRY(h, ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, st));
     }
     CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, st));
@@ -142,7 +143,9 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         if (o.path < CTFMNMF_PATH_AUTO || o.path > CTFMNMF_PATH_PERSISTENT)
             return fail(nullptr, CTFMNMF_EINVAL, "unknown path %d", o.path);
         if (o.wait_timeout_ms < 0) return fail(nullptr, CTFMNMF_EINVAL, "wait_timeout_ms must be >= 0");
-        for (int k = 0; k < 3; ++k)
+        if (o.w_update != CTFMNMF_W_ISS && o.w_update != CTFMNMF_W_IP)
+            return fail(nullptr, CTFMNMF_EINVAL, "unknown w_update %d", o.w_update);
+        for (int k = 0; k < 2; ++k)
             if (o.reserved[k]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
     }
     Shape s;
@@ -169,6 +172,10 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     int fpt = 0, nt = 0;
     if (!ctf::bin_phase_config(M, J, &fpt, &nt))
         return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames is too long for M=%d in one thread block", J, M);
+    const bool ip = o.w_update == CTFMNMF_W_IP;
+    if (ip && M > 4) return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the IP update supports M <= 4 (M=%d)", M);
+    if (ip && o.path == CTFMNMF_PATH_PERSISTENT)
+        return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the IP update runs on the two-kernel path only");
 
     ctfmnmf* h = new (std::nothrow) ctfmnmf;
     if (!h) return fail(nullptr, CTFMNMF_ENOMEM, "host allocation failed");
@@ -196,8 +203,10 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         {(void**)&d.ldm, sizeof(double) * F},
         {(void**)&d.lde, sizeof(int) * F},
         {(void**)&d.sync, sizeof(unsigned) * 32},
+        {(void**)&d.X, ip ? sizeof(float2) * MF * s.Jp : 0},
     };
     for (auto& a : allocs) {
+        if (a.bytes == 0) continue;
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             free_state(h);
@@ -215,6 +224,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
                              cudaMemset(d.P, 0, sizeof(float) * FNJ) != cudaSuccess ||
                              cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
         rc = CTFMNMF_ECUDA;
+    if (rc == CTFMNMF_OK && ip && ctf::configure_ip_bin_phase(s) != cudaSuccess) rc = CTFMNMF_ECUDA;
     if (rc == CTFMNMF_OK && (ctf::configure_bin_phase(s) != cudaSuccess ||
                              ctf::configure_frame_phase() != cudaSuccess ||
                              ctf::launch_init_nmf(s, d, nullptr, nullptr, 0, nullptr) != cudaSuccess ||
@@ -229,7 +239,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     }
     h->skip_cta = -1;
     h->timeout_ns = 1000000ull * (unsigned long long)(o.wait_timeout_ms > 0 ? o.wait_timeout_ms : 2000);
-    h->plan = ctf::plan_persistent(s);
+    if (!ip) h->plan = ctf::plan_persistent(s);
     cudaGetLastError();
     if (o.path == CTFMNMF_PATH_PERSISTENT && !h->plan.ok) {
         free_state(h);
@@ -278,6 +288,9 @@ int ctfmnmf_load_stft(ctfmnmf_t h, const void* X)
     CUDA_TRY(h, ctf::launch_load(h->s, h->d, (const float2*)X, h->stream));
     CUDA_TRY(h, ctf::launch_psd(h->s, h->d, h->stream));
     h->launches += 2;
+    if (h->d.X)       // the IP update demixes the observation itself: keep it (bin-major, padded)
+        CUDA_TRY(h, cudaMemcpyAsync(h->d.X, h->d.Y, sizeof(float2) * (size_t)h->s.F * h->s.M * h->s.Jp,
+                                    cudaMemcpyDeviceToDevice, h->stream));
     int rc = check_flag(h, 1, "X");
     if (rc != CTFMNMF_OK) return rc;
     h->loaded = true;
@@ -456,7 +469,9 @@ int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms)
     int rc = CTFMNMF_OK;
     for (int t = 0; t < n_iter && rc == CTFMNMF_OK; ++t) {
         cudaError_t e = cudaEventRecord(ev[0], h->stream);
-        if (e == cudaSuccess) e = ctf::launch_bin_phase(h->s, h->d, tap0, h->stream);
+        if (e == cudaSuccess)
+            e = h->opt.w_update == CTFMNMF_W_IP ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, h->stream)
+                                                : ctf::launch_bin_phase(h->s, h->d, tap0, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess) e = ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, h->stream);

@@ -233,6 +233,8 @@ int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* o
             return fail_b(CTFMNMF_EINVAL, "all handles need the same v_update and normalize options");
         for (int q = 0; q < k; ++q)
             if (handles[q] == h) return fail_b(CTFMNMF_EINVAL, "a handle appears twice");
+        if (h->opt.w_update != CTFMNMF_W_ISS)
+            return fail_b(CTFMNMF_EUNSUPPORTED, "the batched form runs the ISS update only");
     }
     ctfmnmf_batch* b = new (std::nothrow) ctfmnmf_batch;
     if (!b) return fail_b(CTFMNMF_ENOMEM, "host allocation failed");

@@ -2,7 +2,8 @@
 //
 // Device data layout (one mixture, all resident in HBM):
 //   Y      [F][M][Jp]  complex64  demixed extended rows, bin-major: one bin is one
-//                                 contiguous block of M*Jp*8 bytes (Jp = J rounded up to 4)
+//                                 contiguous block of M*Jp*8 bytes (Jp = J rounded up to 8)
+//   X      [F][M][Jp]  complex64  the loaded observation in the same layout (IP update only)
 //   W      [F][M][M]   complex64  row r of W_i holds w_r^H
 //   logdet [F]         float64    log|det W_i|, tracked by the determinant lemma
 //   T      [N][FBp]    float32    bases, T[n][i][k] at n*FBp + i*B + k (the API shape [N][F][B]
@@ -52,6 +53,7 @@ struct State {
     double* cost_part;  // [F] per-bin cost
     double* cost_out;   // [1]
     float2* staging;    // host-loaded STFT staging [M][F][J]
+    float2* X;          // [F][M][Jp] observation kept for the IP update (null for ISS)
 };
 
 // Launchers (host functions; each enqueues its kernels on `st` and returns the
@@ -62,6 +64,9 @@ cudaError_t launch_init_nmf(const Shape& s, const State& d, const float* T0, con
 cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t configure_bin_phase(const Shape& s);
 cudaError_t launch_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
+// IP update (Eqs. 9-10) in place of the ISS sweep, M <= 4 (bin_phase.cu)
+cudaError_t configure_ip_bin_phase(const Shape& s);
+cudaError_t launch_ip_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
 cudaError_t configure_frame_phase();
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st);

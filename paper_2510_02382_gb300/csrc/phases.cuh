@@ -70,6 +70,172 @@ __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
     return b;
 }
 
+// Complex FP64 helpers of the IP sweep. Every index below is a compile-time constant once
+// the loops over M are unrolled, so the small matrices live in registers; partial pivoting
+// swaps a candidate row into place whenever it is larger (the row of largest magnitude ends
+// up as the pivot, the first one on ties).
+template <int M, int C>
+__device__ __forceinline__ void pivot_rows(double (&ar)[M][C], double (&ai)[M][C], int c)
+{
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        if (p <= c) continue;
+        const double mc = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+        const double mp = ar[p][c] * ar[p][c] + ai[p][c] * ai[p][c];
+        const bool sw = mp > mc;
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            const double xr = ar[c][q], xi = ai[c][q];
+            ar[c][q] = sw ? ar[p][q] : xr;
+            ai[c][q] = sw ? ai[p][q] : xi;
+            ar[p][q] = sw ? xr : ar[p][q];
+            ai[p][q] = sw ? xi : ai[p][q];
+        }
+    }
+}
+
+// Forward elimination below pivot c (columns c..C-1); false if the pivot is zero.
+template <int M, int C>
+__device__ __forceinline__ bool eliminate(double (&ar)[M][C], double (&ai)[M][C], int c)
+{
+    const double m2 = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+    if (!(m2 > 0.0)) return false;
+    const double ir = ar[c][c] / m2, ii = -ai[c][c] / m2;      // 1 / pivot
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        if (p <= c) continue;
+        const double fr = ar[p][c] * ir - ai[p][c] * ii, fi = ar[p][c] * ii + ai[p][c] * ir;
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            if (q < c) continue;
+            ar[p][q] -= fr * ar[c][q] - fi * ai[c][q];
+            ai[p][q] -= fr * ai[c][q] + fi * ar[c][q];
+        }
+    }
+    return true;
+}
+
+// |det A| of a small complex matrix by Gaussian elimination (A is overwritten).
+template <int M>
+__device__ __forceinline__ double abs_det(double (&ar)[M][M], double (&ai)[M][M])
+{
+    double det = 1.0;
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        pivot_rows<M, M>(ar, ai, c);
+        if (!eliminate<M, M>(ar, ai, c)) return 0.0;
+        det *= sqrt(ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c]);
+    }
+    return det;
+}
+
+// The IP sweep of Eqs. 9-10 for one bin, by one thread in FP64: for r = 0..M-1 in order,
+// solve (W Q_r) w = e_r, scale w by (w^H Q_r w)^{-1/2}, set row r of W to w^H.
+// Qs[r][.] holds Q_r as M real diagonal entries, then (re, im) of Q_r[a][b] for a < b in
+// row-major pair order; W (M x M, row r = w_r^H) is updated in place. A singular W Q_r (a
+// bin without energy, or a covariance that FP32 left without full rank) leaves that row
+// unchanged. Returns |det W_new| / |det W_old|.
+template <int M>
+__device__ __forceinline__ double ip_solve(const float* Qs, float2* W)
+{
+    constexpr int NQ = M * M;
+    double wr[M][M], wi[M][M], tr[M][M], ti[M][M];
+#pragma unroll
+    for (int p = 0; p < M; ++p)
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            wr[p][c] = tr[p][c] = W[p * M + c].x;
+            wi[p][c] = ti[p][c] = W[p * M + c].y;
+        }
+    const double det_old = abs_det<M>(tr, ti);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        double qr[M][M], qi[M][M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            qr[a][a] = Qs[r * NQ + a];
+            qi[a][a] = 0.0;
+        }
+        {
+            int pq = 0;
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = 0; b < M; ++b) {
+                    if (b <= a) continue;
+                    qr[a][b] = Qs[r * NQ + M + 2 * pq];
+                    qi[a][b] = Qs[r * NQ + M + 2 * pq + 1];
+                    qr[b][a] = qr[a][b];
+                    qi[b][a] = -qi[a][b];
+                    ++pq;
+                }
+        }
+        double ar[M][M + 1], ai[M][M + 1];               // [W Q_r | e_r]
+#pragma unroll
+        for (int p = 0; p < M; ++p) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double sr = 0.0, si = 0.0;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    sr += wr[p][k] * qr[k][c] - wi[p][k] * qi[k][c];
+                    si += wr[p][k] * qi[k][c] + wi[p][k] * qr[k][c];
+                }
+                ar[p][c] = sr;
+                ai[p][c] = si;
+            }
+            ar[p][M] = p == r ? 1.0 : 0.0;
+            ai[p][M] = 0.0;
+        }
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            pivot_rows<M, M + 1>(ar, ai, c);
+            ok = ok && eliminate<M, M + 1>(ar, ai, c);
+        }
+        if (!ok) continue;
+        double xr[M], xi[M];                             // back substitution
+#pragma unroll
+        for (int p = M - 1; p >= 0; --p) {
+            double sr = ar[p][M], si = ai[p][M];
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                if (q <= p) continue;
+                sr -= ar[p][q] * xr[q] - ai[p][q] * xi[q];
+                si -= ar[p][q] * xi[q] + ai[p][q] * xr[q];
+            }
+            const double den = ar[p][p] * ar[p][p] + ai[p][p] * ai[p][p];
+            xr[p] = (sr * ar[p][p] + si * ai[p][p]) / den;
+            xi[p] = (si * ar[p][p] - sr * ai[p][p]) / den;
+        }
+        double nrm = 0.0;                                // w^H Q_r w (real)
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+                const double ur = qr[a][b] * xr[b] - qi[a][b] * xi[b], ui = qr[a][b] * xi[b] + qi[a][b] * xr[b];
+                nrm += xr[a] * ur + xi[a] * ui;
+            }
+        if (!(nrm > 0.0)) continue;
+        const double sc = 1.0 / sqrt(nrm);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            wr[r][c] = xr[c] * sc;
+            wi[r][c] = -xi[c] * sc;                      // row r = w^H
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < M; ++p)
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            W[p * M + c] = make_float2((float)wr[p][c], (float)wi[p][c]);
+            tr[p][c] = wr[p][c];
+            ti[p][c] = wi[p][c];
+        }
+    const double det_new = abs_det<M>(tr, ti);
+    return det_old > 0.0 ? det_new / det_old : 1.0;
+}
+
 // One CTF-MNMF-ISS bin update (Sec. III) for bin i by group g.
 //   in:  y  = the bin's rows with the pending normalisation applied (frames g.tid + f*g.nt)
 //        wcol (threads g.tid < M) = column g.tid of W_i with the pending scale applied
@@ -79,7 +245,10 @@ __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
 //        P[i] (delayed power, or |y_{(n,0)}|^2 for the tap-0 activation update);
 //        mupart[i][r] = sum_j |y_r(j)|^2;
 //        returns prod_r (1 - z_r), the factor of |det W_i| (Eq. 13).
-template <int M, int FPT, bool GLOBAL, int KB = 16>
+// IP = true replaces the ISS sweep by the IP update of Eqs. 9-10 (M <= 4): the weighted
+// covariances Q_r (Eq. 8) of the kept observation d.X, the sequential solves (ip_solve),
+// then y = W x; the return value is then |det W_new| / |det W_old|.
+template <int M, int FPT, bool GLOBAL, int KB = 16, bool IP = false>
 __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const int i, const Grp& g,
                                           float* gsm, float2 (&y)[M][FPT], float2 (&wcol)[M],
                                           float2* Ydst, float2* Wdst, const float* scale, const int v_tap0)
@@ -133,6 +302,84 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
 
     const float invJ = 1.0f / (float)J;
     float detf = 1.0f;
+    if constexpr (IP) {
+        // ---- IP update (Eqs. 8-10): Q_r from the observation, sequential solves, y = W x
+        static_assert(M <= 4, "the IP update is instantiated for M <= 4");
+        constexpr int NQ = M * M;                    // M real diagonals + M(M-1)/2 complex pairs
+        constexpr int VQ = pow2_at_least(NQ);
+        // [M][NQ] covariances, one slot for the determinant ratio, then W [M][M] (even offset);
+        // 2 + M NQ + 2 M M <= 98 floats fit the basis-update partials (>= 128), free here
+        float* Qs = red2;
+        float2* Wm = reinterpret_cast<float2*>(red2 + ((M * NQ + 2) & ~1));
+        const float2* Xb = d.X + (size_t)i * M * Jp;
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const int j = g.tid + f * g.nt;
+                y[r][f] = j < Jp ? __ldcg(Xb + (size_t)r * Jp + j) : make_float2(0.f, 0.f);
+            }
+        if (g.tid < M) {
+#pragma unroll
+            for (int p = 0; p < M; ++p) Wm[p * M + g.tid] = wcol[p];
+        }
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            float a[VQ];
+#pragma unroll
+            for (int k = 0; k < VQ; ++k) a[k] = 0.f;
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                const float ph = kPhiReg ? phi[r % PR][f % PF]
+                                         : ils[s.row_n[r] * LR + kLPad + min(g.tid + f * g.nt, Jp - 1) - s.row_l[r]];
+                int pq = 0;
+#pragma unroll
+                for (int a0 = 0; a0 < M; ++a0) {
+                    a[a0] = fmaf(ph, abs2(y[a0][f]), a[a0]);
+#pragma unroll
+                    for (int b0 = a0 + 1; b0 < M; ++b0, ++pq) {
+                        const float2 c = cmul_conj(y[a0][f], y[b0][f]);
+                        a[M + 2 * pq] = fmaf(ph, c.x, a[M + 2 * pq]);
+                        a[M + 2 * pq + 1] = fmaf(ph, c.y, a[M + 2 * pq + 1]);
+                    }
+                }
+            }
+            reduce_scatter<VQ>(a, lane);
+            float* rb = red + (r & 1) * NW * 32;
+            if ((lane & (32 / VQ - 1)) == 0) rb[warp * 32 + lane / (32 / VQ)] = a[0];
+            grp_sync(g);
+            if (g.tid < NQ) {
+                float t = 0.f;
+                for (int w = 0; w < NW; ++w) t += rb[w * 32 + g.tid];
+                Qs[r * NQ + g.tid] = t * invJ;
+            }
+        }
+        grp_sync(g);
+        if (g.tid == 0) Qs[M * NQ] = (float)ip_solve<M>(Qs, Wm);   // the slot after Q is free
+        grp_sync(g);
+        detf = Qs[M * NQ];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            float2 xv[M];
+#pragma unroll
+            for (int c = 0; c < M; ++c) xv[c] = y[c][f];
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const float2 w = Wm[r * M + c];
+                    acc.x += w.x * xv[c].x - w.y * xv[c].y;
+                    acc.y += w.x * xv[c].y + w.y * xv[c].x;
+                }
+                y[r][f] = acc;
+            }
+        }
+        if (g.tid < M) {
+#pragma unroll
+            for (int p = 0; p < M; ++p) wcol[p] = Wm[p * M + g.tid];
+        }
+    } else {
     // ---- ISS sweep
 #pragma unroll
     for (int r = 0; r < M; ++r) {
@@ -205,6 +452,7 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
             wcol[r] = make_float2(wr.x * sc, wr.y * sc);
         }
     }
+    }   // ISS
 
     // ---- store the swept rows and W_i, |y|^2 to shared memory, per-row power partials
     float rp[M];

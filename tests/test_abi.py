@@ -72,8 +72,19 @@ def test_create_ex_checks_taps_and_options(lib):
     o.v_update = 7
     assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
     o.v_update = 0
-    o.reserved[2] = 1
+    o.reserved[1] = 1
     assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
+    o.reserved[1] = 0
+    o.w_update = 5
+    assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
+    o.w_update = 1                                             # IP update
+    d5 = api.Dims(5, 2, 3, 4, 8, 32)
+    assert lib.ctfmnmf_create_ex(ctypes.byref(d5), None, ctypes.byref(o), ctypes.byref(h)) == -7
+    assert "M <= 4" in lib.ctfmnmf_last_error(None).decode()
+    o.path = 2                                                 # persistent path
+    assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -7
+    assert "two-kernel" in lib.ctfmnmf_last_error(None).decode()
+    assert h.value is None
     assert lib.ctfmnmf_create(3, 2, 2, 4, 8, 16, None) == -1
 
 
