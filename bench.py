@@ -50,6 +50,8 @@ def parse():
                    help="timed steps of the 64-mixture batched workload (0 skips it)")
     p.add_argument("--fwdbwd-steps", type=int, default=3,
                    help="timed steps of the 16-mixture forward + backward workload (0 skips it)")
+    p.add_argument("--path", default="auto", choices=["auto", "persistent", "two_kernel"],
+                   help="execution path of the plain workload (auto: the library times both)")
     p.add_argument("--ip-steps", type=int, default=3,
                    help="timed steps of the ISS-vs-IP comparison on the plain workload (0 skips it)")
     return p.parse_args()
@@ -67,13 +69,20 @@ def workload_config(spec, l2_note):
             "iterations_per_step": spec.iters, "l2": l2_note, "replicas": "one mixture per rank (seed = rank)"}
 
 
-def csrc_hash():
-    """Short hash of the sources the persistent kernel is compiled from, matched against the
-    one stored with a capture."""
+KERNEL_SOURCES = {   # the CUDA sources each profiled kernel is compiled from (besides the common headers)
+    "persistent_kernel": lambda f: f == "persistent_kernel.cuh" or f.startswith("persistent"),
+    "bin_phase_kernel": lambda f: f == "bin_phase.cu",
+    "frame_phase_kernel": lambda f: f == "kernels.cu",
+}
+
+
+def csrc_hash(kernel="persistent_kernel"):
+    """Short hash of the sources a kernel is compiled from, matched against the one stored
+    with a capture."""
     import hashlib
     d = os.path.join(ROOT, "paper_2510_02382_gb300", "csrc")
-    names = sorted(f for f in os.listdir(d)
-                   if f in ("internal.cuh", "phases.cuh", "persistent_kernel.cuh") or f.startswith("persistent"))
+    pick = KERNEL_SOURCES[kernel]
+    names = sorted(f for f in os.listdir(d) if f in ("internal.cuh", "phases.cuh") or pick(f))
     h = hashlib.sha256()
     for f in names:
         h.update(f.encode())
@@ -82,14 +91,15 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def captured_traffic(kernel_prefix, iters):
-    """DRAM bytes per launch from the committed ncu summary, if it matches these sources."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_prefix}_C2.json")
+def captured_traffic(kernel, launch_iters, want_iters):
+    """DRAM bytes per launch from the committed ncu summary, if it matches these sources and
+    the captured launch ran as many iterations as the timed one."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_C2.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("csrc_sha256_16") != csrc_hash() or iters != 100:
+    if d.get("csrc_sha256_16") != csrc_hash(kernel) or launch_iters != want_iters:
         return None
     return d["dram_bytes_per_launch"]
 
@@ -366,7 +376,7 @@ def run_ours(args):
     mix = synth.make_mixture(spec)
     N, M, F, J, B = spec.N, spec.M, spec.F, spec.J, spec.B
     stream = torch.cuda.current_stream()
-    solver = CTFMNMF(M, N, spec.L, B, F, J, Ln=mix.Ln, stream=stream)
+    solver = CTFMNMF(M, N, spec.L, B, F, J, Ln=mix.Ln, stream=stream, path=args.path)
     X_h = torch.from_numpy(mix.X).pin_memory()
     T0_h = torch.from_numpy(mix.T0).pin_memory()
     V0_h = torch.from_numpy(mix.V0).pin_memory()
@@ -458,7 +468,8 @@ def run_ours(args):
         phase = {"bin_phase_ms": ms_bin, "frame_phase_ms": ms_frame}
     peak, peak_src = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9
-    traffic = captured_traffic("persistent_kernel", iters) if kname == "persistent_kernel" else None
+    traffic = captured_traffic(kname, iters if kname == "persistent_kernel" else 1,
+                               100 if kname == "persistent_kernel" else 1)
     # arithmetic view: about 23 M^2 (ISS) + 12 N B (NMF) flops per bin-frame and iteration
     flops = (23 * M * M + 12 * N * B) * F * J * (iters if kname == "persistent_kernel" else 1)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock

@@ -91,7 +91,10 @@ enum {
  * cooperative launch with a grid-wide barrier between the per-bin and the cross-bin
  * steps (needs B <= 16, J <= 4096 for M <= 4 or J <= 2048 for M = 5..8, and enough
  * co-resident thread blocks). TWO_KERNEL: one launch per step, replayed as a CUDA graph.
- * AUTO: persistent when the shape allows it, else two-kernel. */
+ * AUTO: when the persistent path fits, ctfmnmf_create_ex times a few iterations of each path
+ * on a probe state and keeps the faster (synchronous, a few milliseconds; the handle then
+ * holds the default factors and no STFT, as any new handle); else two-kernel.
+ * ctfmnmf_get_path reports the choice. */
 enum {
     CTFMNMF_PATH_AUTO = 0,
     CTFMNMF_PATH_TWO_KERNEL = 1,

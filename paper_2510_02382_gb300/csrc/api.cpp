@@ -113,6 +113,39 @@ void ctfmnmf_default_options(ctfmnmf_options* opt)
     opt->use_graph = 1;
 }
 
+// AUTO with both paths available: time a few iterations of each on a probe state and keep
+// the faster (neither path wins for every shape: per-iteration launch gaps against the
+// persistent kernel's grid barriers and register budget). Then return the handle to the
+// state of a fresh one (default factors, nothing loaded). Synchronous, a few milliseconds;
+// on any failure the persistent path stays.
+static void choose_path(ctfmnmf* h)
+{
+    constexpr int kIters = 3;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms[2] = {0.f, 0.f};
+    const int paths[2] = {CTFMNMF_PATH_PERSISTENT, CTFMNMF_PATH_TWO_KERNEL};
+    bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+              ctf::launch_probe_fill(h->s, h->d, h->stream) == cudaSuccess;
+    h->loaded = true;
+    for (int q = 0; q < 2 && ok; ++q) {
+        h->path = paths[q];
+        ok = ctfmnmf_iterate(h, kIters) == CTFMNMF_OK &&                 // warm-up (and graph capture)
+             cudaEventRecord(e0, h->stream) == cudaSuccess && ctfmnmf_iterate(h, kIters) == CTFMNMF_OK &&
+             cudaEventRecord(e1, h->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms[q], e0, e1) == cudaSuccess;
+    }
+    h->path = (ok && ms[1] < ms[0]) ? CTFMNMF_PATH_TWO_KERNEL : CTFMNMF_PATH_PERSISTENT;
+    h->loaded = false;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctf::launch_init_nmf(h->s, h->d, nullptr, nullptr, 0, h->stream);
+    ctf::launch_psd(h->s, h->d, h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    h->err[0] = 0;
+    h->launches = 0;
+}
+
 int ctfmnmf_create(int M, int N, int L, int B, int F, int J, ctfmnmf_t* out)
 {
     ctfmnmf_dims d = {M, N, L, B, F, J};
@@ -248,6 +281,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     }
     h->path = (o.path != CTFMNMF_PATH_TWO_KERNEL && h->plan.ok) ? CTFMNMF_PATH_PERSISTENT
                                                                  : CTFMNMF_PATH_TWO_KERNEL;
+    if (o.path == CTFMNMF_PATH_AUTO && h->plan.ok) choose_path(h);
     *out = h;
     return CTFMNMF_OK;
 }

@@ -148,9 +148,12 @@ int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int 
     g->forwarded = false;
     g->launches = 0;
     memset(&g->g, 0, sizeof(g->g));
+    ctfmnmf_options opt;
+    ctfmnmf_default_options(&opt);
+    opt.path = CTFMNMF_PATH_TWO_KERNEL;          // the batched kernels run the iterations
     for (int k = 0; k < batch; ++k) {
         ctfmnmf_t h = nullptr;
-        const int rc = ctfmnmf_create_ex(dims, Ln, nullptr, &h);
+        const int rc = ctfmnmf_create_ex(dims, Ln, &opt, &h);
         if (rc != CTFMNMF_OK) {
             char msg[256];
             snprintf(msg, sizeof(msg), "%s", ctfmnmf_last_error(nullptr));

@@ -62,6 +62,7 @@ cudaError_t launch_load(const Shape& s, const State& d, const float2* X, cudaStr
 cudaError_t launch_init_nmf(const Shape& s, const State& d, const float* T0, const float* V0,
                             uint64_t seed, cudaStream_t st);
 cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st);
+cudaError_t launch_probe_fill(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t configure_bin_phase(const Shape& s);
 cudaError_t launch_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
 // IP update (Eqs. 9-10) in place of the ISS sweep, M <= 4 (bin_phase.cu)

@@ -57,6 +57,36 @@ __device__ __forceinline__ float default_factor(uint64_t seed, uint64_t c)
     return (float)(0.1 + 0.9 * u);
 }
 
+// Probe state for timing the two execution paths: rows with pseudo-random entries in
+// (-1/2, 1/2) + i(-1/2, 1/2) from the splitmix64 counter hash, zero padding frames, W = I,
+// log|det| = 0, no pending scale.
+__global__ void probe_fill_kernel(const Shape s, const State d)
+{
+    const int i = blockIdx.x, m = blockIdx.y;
+    const int M = s.M, J = s.J, Jp = s.Jp;
+    float2* dst = d.Y + ((size_t)i * M + m) * Jp;
+    for (int j = threadIdx.x; j < Jp; j += blockDim.x) {
+        const uint64_t c = ((uint64_t)i * M + m) * (uint64_t)Jp + j;
+        const uint64_t h = splitmix64(0x5eedull * 0x100000000ull + c);
+        const float re = (float)(h >> 40) * (1.0f / 16777216.0f) - 0.5f;
+        const float im = (float)((h >> 16) & 0xffffff) * (1.0f / 16777216.0f) - 0.5f;
+        dst[j] = j < J ? make_float2(re, im) : make_float2(0.f, 0.f);
+    }
+    if ((int)threadIdx.x < M) d.W[((size_t)i * M + m) * M + threadIdx.x] = make_float2(m == (int)threadIdx.x ? 1.f : 0.f, 0.f);
+    if (m == 0 && threadIdx.x == 0) {
+        d.logdet[i] = 0.0;
+        d.ldm[i] = 1.0;
+        d.lde[i] = 0;
+    }
+    if (i == 0 && m == 0 && (int)threadIdx.x < M) d.scale[threadIdx.x] = 1.f;
+}
+
+cudaError_t launch_probe_fill(const Shape& s, const State& d, cudaStream_t st)
+{
+    probe_fill_kernel<<<dim3(s.F, s.M), 256, 0, st>>>(s, d);
+    return cudaGetLastError();
+}
+
 // T0 [N][F][B] -> T [F][N][B]; V0 [N][B][J] -> V [N][B][Jp]. Null source: keep, or the
 // default init when `use_default` is set.
 __global__ void init_nmf_kernel(const Shape s, const State d, const float* __restrict__ T0,

@@ -111,10 +111,28 @@ def test_persistent_and_two_kernel_paths_agree(shape):
 
 
 def test_auto_path_selection():
+    """AUTO times both paths at creation when the persistent one fits, and the handle is
+    then as fresh as any other (the probe leaves no trace in the results)."""
+    import torch
     mix = synth.make_mixture(synth.CONFIGS["C2"])
     s = make_solver(mix)
-    assert s.path == "persistent"
+    assert s.path in ("persistent", "two_kernel")
+    assert s.launch_count() == 0
+    s.load_stft(torch.from_numpy(mix.X).cuda())
+    s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+    s.iterate(1)
+    assert rel_fro(s.get_demixed().cpu().numpy(), run_oracle(mix, 1)["y"]) < 1e-4
     s.close()
+    # without set_init the handle must hold the library's default factors, as a fresh one
+    small = synth.random_case(3, M=3, N=2, F=8, J=96, B=4, Ln=(2, 1))
+    a = make_solver(small)
+    b = make_solver(small, path="two_kernel")
+    for h in (a, b):
+        h.load_stft(torch.from_numpy(small.X).cuda())
+        h.iterate(2)
+    assert rel_fro(a.get_demixed().cpu().numpy(), b.get_demixed().cpu().numpy()) < 1e-5
+    a.close()
+    b.close()
     mix = synth.random_case(1, M=3, N=2, F=4, J=64, B=20, Ln=(2, 1))   # B > 16: two-kernel only
     s = make_solver(mix)
     assert s.path == "two_kernel"
