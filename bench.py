@@ -50,6 +50,8 @@ def parse():
                    help="timed steps of the 64-mixture batched workload (0 skips it)")
     p.add_argument("--fwdbwd-steps", type=int, default=3,
                    help="timed steps of the 16-mixture forward + backward workload (0 skips it)")
+    p.add_argument("--longj-steps", type=int, default=3,
+                   help="timed steps of the long-J workload (F=513, J=16000; 0 skips it)")
     p.add_argument("--path", default="auto", choices=["auto", "persistent", "two_kernel"],
                    help="execution path of the plain workload (auto: the library times both)")
     p.add_argument("--ip-steps", type=int, default=3,
@@ -352,6 +354,50 @@ def ip_leg(args, spec, iters):
             "iss_over_ip": out["iss"] / out["ip"]}
 
 
+def longj_leg(args, peak):
+    """Bins longer than one thread block: the long-J workload (N=2, M=3, L=4, F=513,
+    J=16000, B=10; each bin over a cluster of 8 blocks), 10 iterations per step, CUDA events
+    around ctfmnmf_iterate on the solver's stream, median of the timed steps. Its rows
+    (197 MB) do not fit L2, so no flush is needed; the roofline is the cluster bin phase's
+    own launch time from ctfmnmf_time_phases."""
+    import torch
+    from paper_2510_02382_gb300 import synth
+    from paper_2510_02382_gb300.api import CTFMNMF
+    sp = synth.CONFIGS["L1"]
+    mix = synth.make_mixture(sp)
+    sv = CTFMNMF(sp.M, sp.N, sp.L, sp.B, sp.F, sp.J, Ln=mix.Ln)
+    X = torch.from_numpy(mix.X).cuda()
+    T0 = torch.from_numpy(mix.T0).cuda()
+    V0 = torch.from_numpy(mix.V0).cuda()
+    st = sv.stream
+    ms = []
+    for k in range(args.longj_steps + 1):
+        sv.load_stft(X)
+        sv.set_init(T0, V0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sv.iterate(sp.iters)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if k > 0:
+            ms.append(e0.elapsed_time(e1))
+    ms_bin, ms_frame = sv.time_phases(5)
+    sv.close()
+    t = statistics.median(ms) / 1000.0
+    M, N, F, J, B = sp.M, sp.N, sp.F, sp.J, sp.B
+    it_bytes = 16 * M * F * J + 8 * N * B * (F + J)
+    bin_bytes = 16 * M * F * J + 8 * N * B * F + 4 * N * B * J
+    return {"workload": f"long J: N={N} M={M} L={sp.L} F={F} J={J} B={B}, {sp.iters} iterations per step, "
+                        "bins over clusters of 8 thread blocks", "steps": args.longj_steps,
+            "iterations_per_s": sp.iters / t, "bin_frames_per_s": F * J * sp.iters / t,
+            "ms_per_step": 1000.0 * t, "kernel_times": {"cluster_bin_phase_ms": ms_bin, "frame_phase_ms": ms_frame},
+            "roofline": {"bound": "hbm", "kernel": "cluster_bin_kernel", "achieved": bin_bytes / (ms_bin * 1e-3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": bin_bytes / (ms_bin * 1e-3) / 1e9 / peak,
+                         "algorithmic_bytes_per_launch": bin_bytes},
+            "iteration_roofline_frac": it_bytes * sp.iters / t / 1e9 / peak}
+
+
 def run_ours(args):
     import torch
     from paper_2510_02382_gb300 import synth
@@ -478,6 +524,7 @@ def run_ours(args):
     batched = batched_leg(args, peak) if args.batched_steps > 0 else None
     fwdbwd = fwd_bwd_leg(args, peak) if args.fwdbwd_steps > 0 else None
     ipcmp = ip_leg(args, spec, iters) if args.ip_steps > 0 else None
+    longj = longj_leg(args, peak) if args.longj_steps > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -506,6 +553,7 @@ def run_ours(args):
         "batched": batched,
         "fwd_bwd": fwdbwd,
         "iss_vs_ip": ipcmp,
+        "long_j": longj,
     }
     if batched is not None:
         batched["vs_plain_bin_frames"] = batched["bin_frames_per_s"] / line["bin_frames_per_s"]

@@ -113,8 +113,12 @@ void ctfmnmf_default_options(ctfmnmf_options* opt);
  * (the square model of Sec. II; M=4,6,8 with N=2 gives the paper's Table I).
  * EINVAL if a dimension is <= 0, N > M, M > CTFMNMF_MAX_M, B > CTFMNMF_MAX_B,
  * a derived L_n exceeds L, J <= max L_n, or out is NULL.
- * EUNSUPPORTED if J exceeds 4096 (M <= 4) or 1024 (M = 5..8), or if the options ask for
- * the persistent path and the shape or the device does not allow it.
+ * A bin's frames are processed by one thread block up to J = 4096 (M <= 4) or 1024
+ * (M = 5..8); longer bins are split over a thread-block cluster of 2, 4 or 8 blocks that
+ * combine their sums through distributed shared memory (two-kernel path, ISS update), up
+ * to J = 32768 (M = 2) or 16384 (M = 3..8) and the device's shared memory.
+ * EUNSUPPORTED if J exceeds those limits, or if the options ask for the persistent path
+ * and the shape or the device does not allow it.
  * On success *out receives the handle; on failure *out is set to NULL.
  */
 int ctfmnmf_create(int M, int N, int L, int B, int F, int J, ctfmnmf_t* out);

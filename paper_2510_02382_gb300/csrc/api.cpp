@@ -81,7 +81,9 @@ int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
     const int tap0 = h->opt.v_update == CTFMNMF_V_TAP0;
     const bool ip = h->opt.w_update == CTFMNMF_W_IP;
     for (int t = 0; t < n_iter; ++t) {
-        CUDA_TRY(h, ip ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, st) : ctf::launch_bin_phase(h->s, h->d, tap0, st));
+        CUDA_TRY(h, ip ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, st)
+                       : h->cplan.ok ? ctf::launch_cluster_bin_phase(h->s, h->d, tap0, h->cplan, st)
+                                     : ctf::launch_bin_phase(h->s, h->d, tap0, st));
         CUDA_TRY(h, ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, st));
     }
     CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, st));
@@ -203,9 +205,13 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     if (total != M) return fail(nullptr, CTFMNMF_EINVAL, "taps sum to %d, not M=%d", total, M);
     if (J <= lmax) return fail(nullptr, CTFMNMF_EINVAL, "J=%d frames must exceed the longest tap count %d", J, lmax);
     int fpt = 0, nt = 0;
-    if (!ctf::bin_phase_config(M, J, &fpt, &nt))
-        return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames is too long for M=%d in one thread block", J, M);
+    const bool one_block = ctf::bin_phase_config(M, J, &fpt, &nt);
+    if (!one_block && J > ctf::cluster_max_frames(M))
+        return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames is too long for M=%d (at most %d)", J, M,
+                    ctf::cluster_max_frames(M));
     const bool ip = o.w_update == CTFMNMF_W_IP;
+    if (ip && !one_block)
+        return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the IP update needs a bin's frames in one thread block");
     if (ip && M > 4) return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the IP update supports M <= 4 (M=%d)", M);
     if (ip && o.path == CTFMNMF_PATH_PERSISTENT)
         return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the IP update runs on the two-kernel path only");
@@ -257,8 +263,18 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
                              cudaMemset(d.P, 0, sizeof(float) * FNJ) != cudaSuccess ||
                              cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
         rc = CTFMNMF_ECUDA;
+    if (rc == CTFMNMF_OK && !one_block) {
+        h->cplan = ctf::plan_cluster(s);
+        if (!h->cplan.ok) {
+            free_state(h);
+            delete h;
+            return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames do not fit a cluster of 8 blocks on this device", J);
+        }
+    }
     if (rc == CTFMNMF_OK && ip && ctf::configure_ip_bin_phase(s) != cudaSuccess) rc = CTFMNMF_ECUDA;
-    if (rc == CTFMNMF_OK && (ctf::configure_bin_phase(s) != cudaSuccess ||
+    if (rc == CTFMNMF_OK && (h->cplan.ok ? ctf::configure_cluster_bin_phase(s, h->cplan) : ctf::configure_bin_phase(s)) != cudaSuccess)
+        rc = CTFMNMF_ECUDA;
+    if (rc == CTFMNMF_OK && (
                              ctf::configure_frame_phase() != cudaSuccess ||
                              ctf::launch_init_nmf(s, d, nullptr, nullptr, 0, nullptr) != cudaSuccess ||
                              ctf::launch_psd(s, d, nullptr) != cudaSuccess ||
@@ -505,7 +521,8 @@ int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms)
         cudaError_t e = cudaEventRecord(ev[0], h->stream);
         if (e == cudaSuccess)
             e = h->opt.w_update == CTFMNMF_W_IP ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, h->stream)
-                                                : ctf::launch_bin_phase(h->s, h->d, tap0, h->stream);
+                : h->cplan.ok ? ctf::launch_cluster_bin_phase(h->s, h->d, tap0, h->cplan, h->stream)
+                              : ctf::launch_bin_phase(h->s, h->d, tap0, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess) e = ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, h->stream);

@@ -23,6 +23,7 @@ struct ctfmnmf {
     float2* sepbuf;             // device images for ctfmnmf_get_separated_host (lazy)
     long long launches;         // kernels enqueued so far
     ctf::PersistPlan plan;      // persistent-path plan for this shape on this device
+    ctf::ClusterPlan cplan;     // long-J bin phase (ok when one block cannot hold a bin)
     int path;                   // CTFMNMF_PATH_TWO_KERNEL or CTFMNMF_PATH_PERSISTENT
     int skip_cta;               // test hook: block that skips its first barrier arrival
     unsigned long long timeout_ns;

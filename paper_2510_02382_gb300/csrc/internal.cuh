@@ -113,6 +113,18 @@ int batch_frame_chunk(int B, int BB);
 cudaError_t launch_batch_frame(int BB, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
                                int normalize, cudaStream_t st);
 
+// Long-J bin phase (cluster_bin.cu): one bin over a cluster of cl blocks of nt threads,
+// jc frames each; used when the bin's frames do not fit one block.
+struct ClusterPlan {
+    int ok, cl, jc, nt;
+};
+ClusterPlan plan_cluster(const Shape& s);
+cudaError_t configure_cluster_bin_phase(const Shape& s, const ClusterPlan& p);
+cudaError_t launch_cluster_bin_phase(const Shape& s, const State& d, int v_tap0, const ClusterPlan& p,
+                                     cudaStream_t st);
+// Frames of one bin a cluster of 8 blocks can hold (host rule, before any device query).
+inline int cluster_max_frames(int M) { return 8 * 512 * (M == 2 ? 8 : 4); }
+
 // Set the message that ctfmnmf_last_error(NULL) returns on this thread.
 void set_thread_error(const char* msg);
 

@@ -79,6 +79,8 @@ CONFIGS = {
     "P8": MixSpec("P8", N=2, M=8, L=4, tau=3.0, F=513, J=501, B=3, iters=100),
     # differentiable workload: 20 unrolled iterations, a batch of 16 mixtures (seeds 0..15)
     "C5": MixSpec("C5", N=2, M=3, L=4, tau=3.0, F=257, J=500, B=8, iters=20),
+    # long-J workload: a 256 s recording at hop 256 (16 kHz), beyond one thread block per bin
+    "L1": MixSpec("L1", N=2, M=3, L=4, tau=3.0, F=513, J=16000, B=10, iters=10, snr_db=30.0),
 }
 
 _TAU_BY_L = {2: 1.5, 4: 3.0, 8: 5.0}

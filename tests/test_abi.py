@@ -49,9 +49,9 @@ def _create(lib, M, N, L, Bk, F, J):
     ((3, 2, 1, 4, 8, 16), -1),       # derived taps (2,1) exceed L = 1
     ((3, 2, 2, 4, 8, 2), -1),        # J <= longest tap count
     ((3, 2, 2, 4, -5, 16), -1),      # F <= 0
-    ((4, 2, 2, 4, 8, 5000), -7),     # J too long for one block at M = 4
-    ((8, 2, 4, 4, 8, 1030), -7),     # J too long at M = 8
-    ((5, 2, 3, 4, 8, 1025), -7),     # J too long at M = 5
+    ((4, 2, 2, 4, 8, 16385), -7),    # J too long for a cluster of 8 blocks at M = 4
+    ((8, 2, 4, 4, 8, 16390), -7),    # ... at M = 8
+    ((2, 2, 1, 4, 8, 32769), -7),    # ... at M = 2
 ])
 def test_create_rejects_bad_shapes_on_host(lib, dims, code):
     rc, h = _create(lib, *dims)
@@ -97,9 +97,11 @@ def test_null_handle_calls_fail_cleanly(lib):
 
 
 def test_bin_phase_limits_match_header():
-    # J <= 4096 for M <= 4 and J <= 1024 for M = 5..8 (documented in ctfmnmf_create)
-    text = open(HEADER).read()
-    assert "4096 (M <= 4)" in text and "1024 (M = 5..8)" in text
+    # one block per bin up to J = 4096 (M <= 4) / 1024 (M = 5..8); clusters of up to 8
+    # blocks beyond, up to 32768 (M = 2) / 16384 (M = 3..8) (documented in ctfmnmf_create)
+    text = re.sub(r"\s+", " ", re.sub(r"\n\s*\*", " ", open(HEADER).read()))
+    assert "J = 4096 (M <= 4) or 1024 (M = 5..8)" in text
+    assert "J = 32768 (M = 2) or 16384 (M = 3..8)" in text
 
 
 def test_default_factor_generator_reference_values():
