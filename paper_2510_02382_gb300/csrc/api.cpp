@@ -83,7 +83,7 @@ int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
     for (int t = 0; t < n_iter; ++t) {
         CUDA_TRY(h, ip ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, st)
                        : h->cplan.ok ? ctf::launch_cluster_bin_phase(h->s, h->d, tap0, h->cplan, st)
-                                     : ctf::launch_bin_phase(h->s, h->d, tap0, st));
+                                     : ctf::launch_bin_phase_as(h->s, h->d, tap0, h->bin_fpt, h->bin_nt, st));
         CUDA_TRY(h, ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, st));
     }
     CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, st));
@@ -115,28 +115,61 @@ void ctfmnmf_default_options(ctfmnmf_options* opt)
     opt->use_graph = 1;
 }
 
-// AUTO with both paths available: time a few iterations of each on a probe state and keep
-// the faster (neither path wins for every shape: per-iteration launch gaps against the
-// persistent kernel's grid barriers and register budget). Then return the handle to the
-// state of a fresh one (default factors, nothing loaded). Synchronous, a few milliseconds;
-// on any failure the persistent path stays.
+// AUTO: time a few iterations of each candidate on a probe state and keep the fastest — the
+// persistent kernel (when it fits) and the two-kernel path with each bin-phase shape
+// (frames per thread, threads). Neither path nor shape wins for every mixture: launch gaps
+// against grid barriers and register budgets, block-level reductions against per-thread
+// work. Then return the handle to the state of a fresh one (default factors, nothing
+// loaded). Synchronous, a few milliseconds; on any failure the defaults stay.
 static void choose_path(ctfmnmf* h)
 {
     constexpr int kIters = 3;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float ms[2] = {0.f, 0.f};
-    const int paths[2] = {CTFMNMF_PATH_PERSISTENT, CTFMNMF_PATH_TWO_KERNEL};
+    // candidates: the persistent kernel, then the two-kernel path with each bin-phase shape
+    int fpts[4] = {0, 0, 0, 0}, nts[4] = {0, 0, 0, 0};
+    const int nc = ctf::bin_phase_candidates(h->s.M, h->s.J, fpts, nts);
+    const int def_fpt = h->bin_fpt, def_nt = h->bin_nt;
+    float best = 1e30f;
+    int best_c = -2;                                    // -1: persistent, >= 0: candidate, -2: none
     bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
               ctf::launch_probe_fill(h->s, h->d, h->stream) == cudaSuccess;
     h->loaded = true;
-    for (int q = 0; q < 2 && ok; ++q) {
-        h->path = paths[q];
+    for (int c = h->plan.ok ? -1 : 0; c < nc && ok; ++c) {
+        if (c >= 0 && (ctf::configure_bin_phase_as(h->s, fpts[c], nts[c]) != cudaSuccess)) {
+            cudaGetLastError();
+            continue;
+        }
+        h->path = c < 0 ? CTFMNMF_PATH_PERSISTENT : CTFMNMF_PATH_TWO_KERNEL;
+        if (c >= 0) {
+            h->bin_fpt = fpts[c];
+            h->bin_nt = nts[c];
+        }
+        if (h->graph) {                                 // the graph holds the bin-phase shape
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        float ms = 0.f;
         ok = ctfmnmf_iterate(h, kIters) == CTFMNMF_OK &&                 // warm-up (and graph capture)
              cudaEventRecord(e0, h->stream) == cudaSuccess && ctfmnmf_iterate(h, kIters) == CTFMNMF_OK &&
              cudaEventRecord(e1, h->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-             cudaEventElapsedTime(&ms[q], e0, e1) == cudaSuccess;
+             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (ok && ms < best) {
+            best = ms;
+            best_c = c;
+        }
     }
-    h->path = (ok && ms[1] < ms[0]) ? CTFMNMF_PATH_TWO_KERNEL : CTFMNMF_PATH_PERSISTENT;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->path = best_c >= 0 ? CTFMNMF_PATH_TWO_KERNEL : CTFMNMF_PATH_PERSISTENT;
+    h->bin_fpt = best_c >= 0 ? fpts[best_c] : def_fpt;
+    h->bin_nt = best_c >= 0 ? nts[best_c] : def_nt;
+    if (!ok || best_c == -2) {                          // nothing timed: the defaults
+        h->path = h->plan.ok ? CTFMNMF_PATH_PERSISTENT : CTFMNMF_PATH_TWO_KERNEL;
+        h->bin_fpt = def_fpt;
+        h->bin_nt = def_nt;
+    }
     h->loaded = false;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -286,6 +319,8 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         delete h;
         return fail(nullptr, rc, "device set-up failed: %s", msg);
     }
+    h->bin_fpt = one_block ? fpt : 0;
+    h->bin_nt = one_block ? nt : 0;
     h->skip_cta = -1;
     h->timeout_ns = 1000000ull * (unsigned long long)(o.wait_timeout_ms > 0 ? o.wait_timeout_ms : 2000);
     if (!ip) h->plan = ctf::plan_persistent(s);
@@ -297,7 +332,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     }
     h->path = (o.path != CTFMNMF_PATH_TWO_KERNEL && h->plan.ok) ? CTFMNMF_PATH_PERSISTENT
                                                                  : CTFMNMF_PATH_TWO_KERNEL;
-    if (o.path == CTFMNMF_PATH_AUTO && h->plan.ok) choose_path(h);
+    if (o.path == CTFMNMF_PATH_AUTO && !ip && !h->cplan.ok) choose_path(h);
     *out = h;
     return CTFMNMF_OK;
 }
@@ -522,7 +557,7 @@ int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms)
         if (e == cudaSuccess)
             e = h->opt.w_update == CTFMNMF_W_IP ? ctf::launch_ip_bin_phase(h->s, h->d, tap0, h->stream)
                 : h->cplan.ok ? ctf::launch_cluster_bin_phase(h->s, h->d, tap0, h->cplan, h->stream)
-                              : ctf::launch_bin_phase(h->s, h->d, tap0, h->stream);
+                              : ctf::launch_bin_phase_as(h->s, h->d, tap0, h->bin_fpt, h->bin_nt, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess) e = ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, h->stream);

@@ -84,6 +84,25 @@ size_t bin_phase_smem(const Shape& s)
     return sizeof(float) * (size_t)bin_smem_layout(s.M, s.N, s.Jp, nt).total;
 }
 
+// Every (frames per thread, threads) the bin phase can run this shape with: for each of
+// 1, 2, 4 (up to 256 threads) and 8 (M <= 4, up to 512 threads) the threads that cover J.
+int bin_phase_candidates(int M, int J, int* fpts, int* nts)
+{
+    static const int cands[4] = {1, 2, 4, 8};
+    int k = 0;
+    for (int c = 0; c < 4; ++c) {
+        const int f = cands[c];
+        if (M * f > 32) break;
+        const int cap = f == 8 ? 512 : 256;
+        const int nt = (J + f - 1) / f;
+        if (nt > cap) continue;
+        fpts[k] = f;
+        nts[k] = nt < 64 ? 64 : ((nt + 31) / 32) * 32;
+        ++k;
+    }
+    return k;
+}
+
 int bin_smem_floats(const Shape& s, int nt) { return bin_smem_layout(s.M, s.N, s.Jp, nt).total; }
 
 template <int M, int FPT>
@@ -104,13 +123,15 @@ static cudaError_t launch_mf(const Shape& s, const State& d, int v_tap0, int nt,
         e = cudaFuncGetAttributes(&fa, bin_phase_kernel<M, FPT, kMaxT, kMinB>);
         if (e != cudaSuccess) return e;
         const int dyn_max = optin - (int)fa.sharedSizeBytes;      // static shared memory counts too
-        if (dyn_max < (int)bin_phase_smem(s)) return cudaErrorInvalidValue;
+        if (dyn_max < (int)(sizeof(float) * (size_t)bin_smem_layout(s.M, s.N, s.Jp, nt).total))
+            return cudaErrorInvalidValue;
         return cudaFuncSetAttribute(bin_phase_kernel<M, FPT, kMaxT, kMinB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     }
     // float4 views of the staged rows need 16-byte aligned row starts
     if (s.Jp % 8 != 0 || nt > kMaxT) return cudaErrorInvalidValue;
-    bin_phase_kernel<M, FPT, kMaxT, kMinB><<<s.F, nt, bin_phase_smem(s), st>>>(s, d, v_tap0);
+    const size_t smem = sizeof(float) * (size_t)bin_smem_layout(s.M, s.N, s.Jp, nt).total;
+    bin_phase_kernel<M, FPT, kMaxT, kMinB><<<s.F, nt, smem, st>>>(s, d, v_tap0);
     return cudaGetLastError();
 }
 
@@ -128,10 +149,10 @@ static cudaError_t launch_m(const Shape& s, const State& d, int v_tap0, int fpt,
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t dispatch(const Shape& s, const State& d, int v_tap0, cudaStream_t st, bool cfg)
+static cudaError_t dispatch(const Shape& s, const State& d, int v_tap0, cudaStream_t st, bool cfg, int fpt = 0,
+                            int nt = 0)
 {
-    int fpt = 0, nt = 0;
-    if (!bin_phase_config(s.M, s.J, &fpt, &nt)) return cudaErrorInvalidValue;
+    if (fpt == 0 && !bin_phase_config(s.M, s.J, &fpt, &nt)) return cudaErrorInvalidValue;
     switch (s.M) {
         case 2: return launch_m<2>(s, d, v_tap0, fpt, nt, st, cfg);
         case 3: return launch_m<3>(s, d, v_tap0, fpt, nt, st, cfg);
@@ -155,6 +176,17 @@ cudaError_t configure_bin_phase(const Shape& s)
 cudaError_t launch_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st)
 {
     return dispatch(s, d, v_tap0, st, false);
+}
+
+cudaError_t configure_bin_phase_as(const Shape& s, int fpt, int nt)
+{
+    State none = {};
+    return dispatch(s, none, 0, nullptr, true, fpt, nt);
+}
+
+cudaError_t launch_bin_phase_as(const Shape& s, const State& d, int v_tap0, int fpt, int nt, cudaStream_t st)
+{
+    return dispatch(s, d, v_tap0, st, false, fpt, nt);
 }
 
 template <int M, int FPT>

@@ -24,6 +24,7 @@ struct ctfmnmf {
     long long launches;         // kernels enqueued so far
     ctf::PersistPlan plan;      // persistent-path plan for this shape on this device
     ctf::ClusterPlan cplan;     // long-J bin phase (ok when one block cannot hold a bin)
+    int bin_fpt, bin_nt;        // frames per thread and threads of the bin phase (0: default)
     int path;                   // CTFMNMF_PATH_TWO_KERNEL or CTFMNMF_PATH_PERSISTENT
     int skip_cta;               // test hook: block that skips its first barrier arrival
     unsigned long long timeout_ns;

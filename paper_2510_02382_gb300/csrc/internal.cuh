@@ -65,6 +65,10 @@ cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t launch_probe_fill(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t configure_bin_phase(const Shape& s);
 cudaError_t launch_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
+// The bin phase with an explicit (frames per thread, threads) from bin_phase_candidates.
+int bin_phase_candidates(int M, int J, int* fpts, int* nts);
+cudaError_t configure_bin_phase_as(const Shape& s, int fpt, int nt);
+cudaError_t launch_bin_phase_as(const Shape& s, const State& d, int v_tap0, int fpt, int nt, cudaStream_t st);
 // IP update (Eqs. 9-10) in place of the ISS sweep, M <= 4 (bin_phase.cu)
 cudaError_t configure_ip_bin_phase(const Shape& s);
 cudaError_t launch_ip_bin_phase(const Shape& s, const State& d, int v_tap0, cudaStream_t st);
