@@ -124,6 +124,8 @@ int make_plan(const std::vector<ctfmnmf*>& hs, int pref, bool merge, Plan* out)
 
 }  // namespace
 
+constexpr int kBranches = 4;     // concurrent bin-class branches per iteration
+
 struct ctfmnmf_batch {
     std::vector<ctfmnmf*> hs;
     MixDesc* dmix;              // device [count]
@@ -134,9 +136,22 @@ struct ctfmnmf_batch {
     cudaGraphExec_t graph;
     int graph_iters;
     long long launches;
+    // the bin classes of one iteration touch disjoint mixtures: they run as parallel
+    // branches (side streams forked from and joined to the launching stream by events)
+    cudaStream_t side[kBranches];
+    cudaEvent_t fork, join[kBranches];
 };
 
 namespace {
+
+void release_branches(ctfmnmf_batch* b)
+{
+    for (int k = 0; k < kBranches; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+}
 
 int fail_b(int code, const char* fmt, const char* what = "")
 {
@@ -148,10 +163,24 @@ int fail_b(int code, const char* fmt, const char* what = "")
 
 cudaError_t enqueue_batch(ctfmnmf_batch* b, const Plan& p, int n_iter, cudaStream_t st)
 {
+    const int nb = (int)p.bins.size();
+    const int K = nb < kBranches ? nb : kBranches;
     for (int t = 0; t < n_iter; ++t) {
-        for (const auto& c : p.bins) {
-            cudaError_t e = ctf::launch_batch_bin(c, b->dmix, b->v_tap0, st, false);
+        if (K > 1) {
+            // fork: class c on branch c % K; join before the frame phase, which reads every
+            // mixture's bin-phase output
+            cudaError_t e = cudaEventRecord(b->fork, st);
+            for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+            for (int c = 0; c < nb && e == cudaSuccess; ++c)
+                e = ctf::launch_batch_bin(p.bins[c], b->dmix, b->v_tap0, b->side[c % K], false);
+            for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaEventRecord(b->join[k], b->side[k]);
+            for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(st, b->join[k], 0);
             if (e != cudaSuccess) return e;
+        } else {
+            for (const auto& c : p.bins) {
+                cudaError_t e = ctf::launch_batch_bin(c, b->dmix, b->v_tap0, st, false);
+                if (e != cudaSuccess) return e;
+            }
         }
         for (const auto& f : p.frames) {
             cudaError_t e = ctf::launch_batch_frame(f.BB, b->dmix, f.work, f.blocks, b->v_tap0, b->normalize, st);
@@ -241,6 +270,11 @@ int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* o
     b->hs.assign(handles, handles + count);
     b->dmix = nullptr;
     b->capture = nullptr;
+    b->fork = nullptr;
+    for (int k = 0; k < kBranches; ++k) {
+        b->side[k] = nullptr;
+        b->join[k] = nullptr;
+    }
     b->graph = nullptr;
     b->graph_iters = 0;
     b->launches = 0;
@@ -255,10 +289,17 @@ int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* o
     int rc = CTFMNMF_OK;
     if (cudaMalloc((void**)&b->dmix, sizeof(MixDesc) * count) != cudaSuccess ||
         cudaMemcpy(b->dmix, mix.data(), sizeof(MixDesc) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         rc = fail_b(CTFMNMF_ENOMEM, "device set-up of the batch failed");
     }
+    for (int k = 0; k < kBranches && rc == CTFMNMF_OK; ++k)
+        if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail_b(CTFMNMF_ENOMEM, "device set-up of the batch failed");
+        }
     // ---- autotune: candidates (preference, merge), two timed iterations each
     cudaStream_t st = b->hs[0]->stream;
     Saved sv;
@@ -303,6 +344,7 @@ int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* o
         free_plan(b->plan);
         if (b->dmix) cudaFree(b->dmix);
         if (b->capture) cudaStreamDestroy(b->capture);
+        release_branches(b);
         delete b;
         return rc;
     }
@@ -390,6 +432,7 @@ int ctfmnmf_batch_destroy(ctfmnmf_batch_t b)
     free_plan(b->plan);
     if (b->dmix) cudaFree(b->dmix);
     if (b->capture) cudaStreamDestroy(b->capture);
+    release_branches(b);
     delete b;
     return CTFMNMF_OK;
 }
