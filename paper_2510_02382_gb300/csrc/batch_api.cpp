@@ -64,19 +64,20 @@ bool bin_shape(int M, int J, int pref, int* fpt, int* nt)
 int make_plan(const std::vector<ctfmnmf*>& hs, int pref, bool merge, Plan* out)
 {
     // key -> list of (mixture, F) ; key = (M, fpt, nt) with nt = 0 when merged
-    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
     std::vector<int> mix_nt(hs.size());
     for (size_t b = 0; b < hs.size(); ++b) {
         int fpt = 0, nt = 0;
         if (!bin_shape(hs[b]->s.M, hs[b]->s.J, pref, &fpt, &nt)) return CTFMNMF_EUNSUPPORTED;
         mix_nt[b] = nt;
-        groups[std::make_tuple(hs[b]->s.M, fpt, merge ? 0 : nt)].push_back((int)b);
+        groups[std::make_tuple(hs[b]->s.M, fpt, merge ? 0 : nt, ctf::bases_class(hs[b]->s.B))].push_back((int)b);
     }
     for (auto& kv : groups) {
         BatchClass c;
         memset(&c, 0, sizeof(c));
         c.M = std::get<0>(kv.first);
         c.fpt = std::get<1>(kv.first);
+        c.kb = std::get<3>(kv.first);
         int nt = 0;
         size_t smem = 0;
         std::vector<int2> work;

@@ -1,0 +1,16 @@
+// Bin-phase instantiations for M = 2 extended rows.
+#include "bin_phase_kernels.cuh"
+
+namespace ctf {
+
+cudaError_t bin_phase_m2(const Shape& s, const State& d, int v_tap0, int fpt, int nt, cudaStream_t st, bool cfg)
+{
+    return launch_m<2>(s, d, v_tap0, fpt, nt, st, cfg);
+}
+
+cudaError_t ip_bin_phase_m2(const Shape& s, const State& d, int v_tap0, int fpt, int nt, cudaStream_t st, bool cfg)
+{
+    return launch_ip_m<2>(s, d, v_tap0, fpt, nt, st, cfg);
+}
+
+}  // namespace ctf

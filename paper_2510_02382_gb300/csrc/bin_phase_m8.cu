@@ -1,0 +1,11 @@
+// Bin-phase instantiations for M = 8 extended rows.
+#include "bin_phase_kernels.cuh"
+
+namespace ctf {
+
+cudaError_t bin_phase_m8(const Shape& s, const State& d, int v_tap0, int fpt, int nt, cudaStream_t st, bool cfg)
+{
+    return launch_m<8>(s, d, v_tap0, fpt, nt, st, cfg);
+}
+
+}  // namespace ctf

@@ -106,11 +106,13 @@ struct MixDesc {
 };
 struct BatchClass {
     int M, fpt, nt, blocks;
+    int kb;            // bases per basis-MU pass (4, 8, 10, 16), covering every B of the class
     size_t smem;
     int2* work;        // device [blocks]
 };
 cudaError_t launch_batch_bin(const BatchClass& c, const MixDesc* mixes, int v_tap0, cudaStream_t st,
                              bool configure);
+int bases_class(int B);   // 4, 8, 10 or 16: the basis-MU pass width for B bases (bin_phase.cu)
 cudaError_t configure_batch_frame();
 int batch_frame_class(int B);
 int batch_frame_chunk(int B, int BB);

@@ -249,7 +249,9 @@ def test_host_buffers_match_device_buffers():
     sp = mix.spec
     res = []
     for host in (False, True):
-        s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln)
+        # one fixed path: AUTO times its candidates, so two handles may pick different
+        # bin-phase shapes and sum in different orders
+        s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln, path="two_kernel")
         X = torch.from_numpy(mix.X)
         s.load_stft(X if host else X.cuda())
         s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
