@@ -59,6 +59,17 @@ def parse():
     return p.parse_args()
 
 
+def job_throughput(local_ms, world, iters, steps, dist=None, device="cpu"):
+    """Whole-job rate: this rank's elapsed milliseconds maxed over the ranks (the job ends
+    with its slowest rank), units = world * iters * steps. Returns (rate per second, max ms)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * iters * steps / (ms / 1000.0), ms
+
+
 def spec_for(rank):
     from paper_2510_02382_gb300 import synth
     return synth.scaled(synth.CONFIGS[WORKLOAD], seed=rank)
@@ -454,11 +465,7 @@ def run_ours(args):
     launches = solver.launch_count() - launches0
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     clocks = sampler.stop() if sampler else None
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * iters * args.steps / (total_ms / 1000.0)
+    value, total_ms = job_throughput(total_ms, world, iters, args.steps, dist, "cuda")
 
     # ---- end to end through host buffers
     out_h = torch.empty((N, M, F, J), dtype=torch.complex64).pin_memory()
@@ -484,10 +491,7 @@ def run_ours(args):
         ev2[k][1].record(stream)
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * iters * e2e_steps / (float(t.item()) / 1000.0)
+    e2e_value, _ = job_throughput(e2e_ms, world, iters, e2e_steps, dist, "cuda")
     h2d = X_h.numel() * 8 + T0_h.numel() * 4 + V0_h.numel() * 4
     d2h = out_h.numel() * 8
 
