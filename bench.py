@@ -54,6 +54,8 @@ def parse():
                    help="timed steps of the long-J workload (F=513, J=16000; 0 skips it)")
     p.add_argument("--path", default="auto", choices=["auto", "persistent", "two_kernel"],
                    help="execution path of the plain workload (auto: the library times both)")
+    p.add_argument("--bin-fpt", type=int, default=0,
+                   help="frames per thread of the two-kernel bin phase (0: the library's choice)")
     p.add_argument("--ip-steps", type=int, default=3,
                    help="timed steps of the ISS-vs-IP comparison on the plain workload (0 skips it)")
     return p.parse_args()
@@ -433,7 +435,7 @@ def run_ours(args):
     mix = synth.make_mixture(spec)
     N, M, F, J, B = spec.N, spec.M, spec.F, spec.J, spec.B
     stream = torch.cuda.current_stream()
-    solver = CTFMNMF(M, N, spec.L, B, F, J, Ln=mix.Ln, stream=stream, path=args.path)
+    solver = CTFMNMF(M, N, spec.L, B, F, J, Ln=mix.Ln, stream=stream, path=args.path, bin_fpt=args.bin_fpt)
     X_h = torch.from_numpy(mix.X).pin_memory()
     T0_h = torch.from_numpy(mix.T0).pin_memory()
     V0_h = torch.from_numpy(mix.V0).pin_memory()
@@ -524,6 +526,7 @@ def run_ours(args):
     flops = (23 * M * M + 12 * N * B) * F * J * (iters if kname == "persistent_kernel" else 1)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
     solver_path = solver.path
+    bin_fpt, bin_nt = solver.bin_shape()
     solver.close()
     batched = batched_leg(args, peak) if args.batched_steps > 0 else None
     fwdbwd = fwd_bwd_leg(args, peak) if args.fwdbwd_steps > 0 else None
@@ -548,6 +551,7 @@ def run_ours(args):
                      "alu": {"achieved_tflops": flops / (kms * 1e-3) / 1e12, "peak_tflops": fp32_peak,
                              "frac": flops / (kms * 1e-3) / 1e12 / fp32_peak}},
         "path": solver_path,
+        "bin_shape": {"frames_per_thread": bin_fpt, "threads": bin_nt},
         "kernel_times": phase,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -78,7 +78,11 @@ typedef struct ctfmnmf_options {
                                   CTFMNMF_W_IP: the IP update of Eqs. 9-10 that ISS
                                   replaces (M <= 4, two-kernel path only, not in a batch;
                                   keeps a copy of X, 8*M*F*J more bytes)                */
-    int reserved[2];           /* must be zero                                          */
+    int bin_fpt;               /* frames per thread of the two-kernel bin phase: 1, 2, 4
+                                  or 8 (M <= 4) when it fits J; 0 (default): with path
+                                  AUTO timed among the candidates, else the fewest that
+                                  fit. EUNSUPPORTED if the value cannot run this shape  */
+    int reserved[1];           /* must be zero                                          */
 } ctfmnmf_options;
 
 /* Demixing updates (ctfmnmf_options.w_update). */
@@ -344,6 +348,10 @@ int ctfmnmf_get_launch_count(ctfmnmf_t h, long long* count);
 /* Which path ctfmnmf_iterate takes for this handle: CTFMNMF_PATH_TWO_KERNEL or
  * CTFMNMF_PATH_PERSISTENT, written to *path (host). */
 int ctfmnmf_get_path(ctfmnmf_t h, int* path);
+
+/* The two-kernel bin phase's frames per thread and threads per block for this handle (both
+ * 0 when its bins run over thread-block clusters), written to *fpt and *threads (host). */
+int ctfmnmf_get_bin_shape(ctfmnmf_t h, int* fpt, int* threads);
 
 /*
  * Persistent path only: run one launch of n_iter >= 1 iterations with a CUDA event pair

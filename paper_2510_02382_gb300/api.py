@@ -27,7 +27,7 @@ class Dims(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("v_update", c_int), ("normalize", c_int), ("use_graph", c_int), ("path", c_int),
-                ("wait_timeout_ms", c_int), ("w_update", c_int), ("reserved", c_int * 2)]
+                ("wait_timeout_ms", c_int), ("w_update", c_int), ("bin_fpt", c_int), ("reserved", c_int * 1)]
 
 
 PATHS = {"auto": 0, "two_kernel": 1, "persistent": 2}
@@ -65,6 +65,7 @@ _SIGS = {
     "ctfmnmf_get_launch_count": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_synchronize": (c_int, [c_void_p]),
     "ctfmnmf_get_path": (c_int, [c_void_p, c_void_p]),
+    "ctfmnmf_get_bin_shape": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ctfmnmf_time_persistent": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_debug_skip_arrival": (c_int, [c_void_p, c_int]),
     "ctfmnmf_cost_noalloc": (c_int, [c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -255,7 +256,7 @@ class CTFMNMF:
     def __init__(self, M: int, N: int, L: int, B: int, F: int, J: int,
                  Ln: Optional[Sequence[int]] = None, v_update: str = "all_taps",
                  normalize: bool = True, use_graph: bool = True, path: str = "auto",
-                 wait_timeout_ms: int = 0, w_update: str = "iss", stream=None):
+                 wait_timeout_ms: int = 0, w_update: str = "iss", bin_fpt: int = 0, stream=None):
         import torch
         self.M, self.N, self.L, self.B, self.F, self.J = M, N, L, B, F, J
         d = Dims(M, N, L, B, F, J)
@@ -267,6 +268,7 @@ class CTFMNMF:
         o.path = PATHS[path]
         o.wait_timeout_ms = int(wait_timeout_ms)
         o.w_update = {"iss": W_ISS, "ip": W_IP}[w_update]
+        o.bin_fpt = int(bin_fpt)
         ln_arr = (c_int * N)(*Ln) if Ln is not None else None
         h = c_void_p()
         rc = lib().ctfmnmf_create_ex(ctypes.byref(d), ln_arr, ctypes.byref(o), ctypes.byref(h))
@@ -385,6 +387,12 @@ class CTFMNMF:
         out = ctypes.c_longlong()
         _check(lib().ctfmnmf_get_launch_count(self._h, ctypes.byref(out)), self._h)
         return int(out.value)
+
+    def bin_shape(self):
+        """(frames per thread, threads) of the two-kernel bin phase; (0, 0) for cluster bins."""
+        f, t = c_int(), c_int()
+        _check(lib().ctfmnmf_get_bin_shape(self._h, ctypes.byref(f), ctypes.byref(t)), self._h)
+        return f.value, t.value
 
     @staticmethod
     def _expect(t, shape, dtype, cuda=None):

@@ -127,8 +127,13 @@ static void choose_path(ctfmnmf* h)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // candidates: the persistent kernel, then the two-kernel path with each bin-phase shape
     int fpts[4] = {0, 0, 0, 0}, nts[4] = {0, 0, 0, 0};
-    const int nc = ctf::bin_phase_candidates(h->s.M, h->s.J, fpts, nts);
+    int nc = ctf::bin_phase_candidates(h->s.M, h->s.J, fpts, nts);
     const int def_fpt = h->bin_fpt, def_nt = h->bin_nt;
+    if (h->opt.bin_fpt != 0) {                          // a forced shape is the only candidate
+        fpts[0] = def_fpt;
+        nts[0] = def_nt;
+        nc = 1;
+    }
     float best = 1e30f;
     int best_c = -2;                                    // -1: persistent, >= 0: candidate, -2: none
     bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
@@ -213,8 +218,9 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         if (o.wait_timeout_ms < 0) return fail(nullptr, CTFMNMF_EINVAL, "wait_timeout_ms must be >= 0");
         if (o.w_update != CTFMNMF_W_ISS && o.w_update != CTFMNMF_W_IP)
             return fail(nullptr, CTFMNMF_EINVAL, "unknown w_update %d", o.w_update);
-        for (int k = 0; k < 2; ++k)
-            if (o.reserved[k]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
+        if (o.reserved[0]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
+        if (o.bin_fpt != 0 && o.bin_fpt != 1 && o.bin_fpt != 2 && o.bin_fpt != 4 && o.bin_fpt != 8)
+            return fail(nullptr, CTFMNMF_EINVAL, "bin_fpt must be 0, 1, 2, 4 or 8");
     }
     Shape s;
     memset(&s, 0, sizeof(s));
@@ -242,6 +248,16 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     if (!one_block && J > ctf::cluster_max_frames(M))
         return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames is too long for M=%d (at most %d)", J, M,
                     ctf::cluster_max_frames(M));
+    if (o.bin_fpt != 0) {                          // a forced bin-phase shape must be a candidate
+        int fpts[4], nts[4];
+        const int nc = ctf::bin_phase_candidates(M, J, fpts, nts);
+        int k = 0;
+        while (k < nc && fpts[k] != o.bin_fpt) ++k;
+        if (k == nc)
+            return fail(nullptr, CTFMNMF_EUNSUPPORTED, "bin_fpt=%d cannot run J=%d frames with M=%d", o.bin_fpt, J, M);
+        fpt = fpts[k];
+        nt = nts[k];
+    }
     const bool ip = o.w_update == CTFMNMF_W_IP;
     if (ip && !one_block)
         return fail(nullptr, CTFMNMF_EUNSUPPORTED, "the IP update needs a bin's frames in one thread block");
@@ -305,7 +321,8 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         }
     }
     if (rc == CTFMNMF_OK && ip && ctf::configure_ip_bin_phase(s) != cudaSuccess) rc = CTFMNMF_ECUDA;
-    if (rc == CTFMNMF_OK && (h->cplan.ok ? ctf::configure_cluster_bin_phase(s, h->cplan) : ctf::configure_bin_phase(s)) != cudaSuccess)
+    if (rc == CTFMNMF_OK && (h->cplan.ok ? ctf::configure_cluster_bin_phase(s, h->cplan)
+                                         : ctf::configure_bin_phase_as(s, fpt, nt)) != cudaSuccess)
         rc = CTFMNMF_ECUDA;
     if (rc == CTFMNMF_OK && (
                              ctf::configure_frame_phase() != cudaSuccess ||
@@ -592,6 +609,15 @@ int ctfmnmf_get_path(ctfmnmf_t h, int* path)
     if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
     if (!path) return fail(h, CTFMNMF_EINVAL, "path is NULL");
     *path = h->path;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_get_bin_shape(ctfmnmf_t h, int* fpt, int* threads)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!fpt || !threads) return fail(h, CTFMNMF_EINVAL, "need two outputs");
+    *fpt = h->cplan.ok ? 0 : h->bin_fpt;
+    *threads = h->cplan.ok ? 0 : h->bin_nt;
     return CTFMNMF_OK;
 }
 

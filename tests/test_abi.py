@@ -72,9 +72,16 @@ def test_create_ex_checks_taps_and_options(lib):
     o.v_update = 7
     assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
     o.v_update = 0
-    o.reserved[1] = 1
+    o.reserved[0] = 1
     assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
-    o.reserved[1] = 0
+    o.reserved[0] = 0
+    o.bin_fpt = 3                                              # not 0, 1, 2, 4, 8
+    assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
+    o.bin_fpt = 1                                              # J = 32 at one frame per thread fits
+    o.bin_fpt = 8
+    d5 = api.Dims(5, 2, 3, 4, 8, 32)
+    assert lib.ctfmnmf_create_ex(ctypes.byref(d5), None, ctypes.byref(o), ctypes.byref(h)) == -7   # 8 needs M <= 4
+    o.bin_fpt = 0
     o.w_update = 5
     assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
     o.w_update = 1                                             # IP update
