@@ -297,3 +297,23 @@ def test_c3_full_size_1_iteration(path):
     sp = mix.spec
     ok, err = cost_close(g["cost"], r["cost"], 1e-5, sp.F, sp.J, sp.M)
     assert ok, err
+
+
+@pytest.mark.parametrize("fpt", [1, 2, 4, 8])
+def test_every_bin_phase_shape_matches_oracle(fpt):
+    """ctfmnmf_options.bin_fpt forces each two-kernel bin-phase shape AUTO chooses among;
+    each must give the oracle's result (they differ only in how frames map to threads)."""
+    import torch
+    from paper_2510_02382_gb300.api import CTFMNMF
+    mix = synth.random_case(77, M=3, N=2, F=7, J=200, B=10, Ln=(2, 1))
+    sp = mix.spec
+    s = CTFMNMF(sp.M, sp.N, 2, sp.B, sp.F, sp.J, Ln=mix.Ln, path="two_kernel", bin_fpt=fpt)
+    assert s.bin_shape()[0] == fpt
+    s.load_stft(torch.from_numpy(mix.X).cuda())
+    s.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+    s.iterate(3)
+    ref = run_oracle(mix, 3)
+    assert rel_fro(s.get_demixed().cpu().numpy(), ref["y"]) < 1e-4
+    ok, err = cost_close(s.cost(), ref["cost"], 1e-5, sp.F, sp.J, sp.M)
+    assert ok, err
+    s.close()
