@@ -216,6 +216,20 @@ int ctfmnmf_get_logdet(ctfmnmf_t h, double* logdet);
 /* NMF factors: device pointers, float32 T [N][F][B] and V [N][B][J]; either may be NULL. */
 int ctfmnmf_get_nmf(ctfmnmf_t h, float* T, float* V);
 
+/*
+ * Checkpoint/resume: restore a state exported with the getters above — Y [M][F][J]
+ * complex64 (ctfmnmf_get_demixed), W [F][M][M] complex64 (ctfmnmf_get_demix_matrix),
+ * T [N][F][B] and V [N][B][J] float32 (ctfmnmf_get_nmf), logdet [F] float64
+ * (ctfmnmf_get_logdet); device pointers, read, none may be NULL. The handle then iterates
+ * on from that state as the exporting handle would, to FP32 rounding (it forms 1/lambda
+ * afresh from T and V). Synchronises the stream (the
+ * rows are checked for NaN/Inf: ENONFINITE). The observation X is not part of the state:
+ * a handle with the IP update keeps the X of its last ctfmnmf_load_stft and gives ESTATE
+ * without one.
+ */
+int ctfmnmf_set_state(ctfmnmf_t h, const void* Y, const void* W, const float* T, const float* V,
+                      const double* logdet);
+
 /* ---- batched form: many mixtures advanced together ---- */
 
 typedef struct ctfmnmf_batch* ctfmnmf_batch_t;
@@ -248,6 +262,20 @@ int ctfmnmf_batch_time(ctfmnmf_batch_t b, int n_iter, double* ms);
 /* Diagnostic: info[5] (host) = {mixtures, bin classes, frame classes, chosen candidate
  * plan (2 * eight-frames-preferred + merged-classes), kernels launched so far}. */
 int ctfmnmf_batch_info(ctfmnmf_batch_t b, int* info);
+
+/*
+ * Ragged buffers for the whole batch: one device buffer holding every mixture's block, and
+ * offsets[k] (host array, in elements of the buffer's type) of mixture k's block.
+ *   ctfmnmf_batch_load_stft:     X blocks [M][F][J] complex64 (as ctfmnmf_load_stft, each
+ *                                checked for NaN/Inf; synchronises once).
+ *   ctfmnmf_batch_set_init:      T0 blocks [N][F][B], V0 blocks [N][B][J] float32 (either
+ *                                buffer may be NULL: that factor stays).
+ *   ctfmnmf_batch_get_separated: images [N][M][F][J] complex64 (written, asynchronous).
+ */
+int ctfmnmf_batch_load_stft(ctfmnmf_batch_t b, const void* X, const long long* offsets);
+int ctfmnmf_batch_set_init(ctfmnmf_batch_t b, const float* T0, const long long* t_offsets, const float* V0,
+                           const long long* v_offsets);
+int ctfmnmf_batch_get_separated(ctfmnmf_batch_t b, void* C, const long long* offsets);
 
 /* Release the batch (not its handles). b may be NULL. */
 int ctfmnmf_batch_destroy(ctfmnmf_batch_t b);

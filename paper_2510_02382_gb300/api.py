@@ -61,6 +61,7 @@ _SIGS = {
     "ctfmnmf_get_demix_matrix": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_get_logdet": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_get_nmf": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ctfmnmf_time_phases": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_get_launch_count": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_synchronize": (c_int, [c_void_p]),
@@ -75,6 +76,9 @@ _SIGS = {
     "ctfmnmf_batch_time": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_batch_info": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_batch_destroy": (c_int, [c_void_p]),
+    "ctfmnmf_batch_load_stft": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_batch_set_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ctfmnmf_batch_get_separated": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ctfmnmf_grad_create": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     "ctfmnmf_grad_set_stream": (c_int, [c_void_p, c_void_p]),
     "ctfmnmf_grad_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -134,6 +138,22 @@ class Batch:
         ms = c_double()
         _check(lib().ctfmnmf_batch_time(self._h, int(n_iter), ctypes.byref(ms)), None)
         return ms.value
+
+    def load_stft(self, X, offsets):
+        """All mixtures' X from one complex64 device buffer; offsets[k] = element offset of
+        mixture k's [M][F][J] block."""
+        offs = (ctypes.c_longlong * len(self.solvers))(*[int(o) for o in offsets])
+        _check(lib().ctfmnmf_batch_load_stft(self._h, c_void_p(X.data_ptr()), offs), None)
+
+    def set_init(self, T0, t_offsets, V0, v_offsets):
+        to = (ctypes.c_longlong * len(self.solvers))(*[int(o) for o in t_offsets])
+        vo = (ctypes.c_longlong * len(self.solvers))(*[int(o) for o in v_offsets])
+        _check(lib().ctfmnmf_batch_set_init(self._h, _ptr(T0), to, _ptr(V0), vo), None)
+
+    def get_separated(self, C, offsets):
+        offs = (ctypes.c_longlong * len(self.solvers))(*[int(o) for o in offsets])
+        _check(lib().ctfmnmf_batch_get_separated(self._h, c_void_p(C.data_ptr()), offs), None)
+        return C
 
     def info(self):
         out = (c_int * 5)()
@@ -320,6 +340,23 @@ class CTFMNMF:
 
     def iterate(self, n_iter: int):
         _check(lib().ctfmnmf_iterate(self._h, int(n_iter)), self._h)
+
+    def get_state(self):
+        """The iteration state as tensors (checkpoint): Y [M][F][J] complex64, W [F][M][M]
+        complex64, T [N][F][B], V [N][B][J] float32, logdet [F] float64."""
+        T, V = self.get_nmf()
+        return {"Y": self.get_demixed(), "W": self.get_demix_matrix(), "T": T, "V": V, "logdet": self.get_logdet()}
+
+    def set_state(self, st):
+        """Resume from a state returned by get_state (device tensors)."""
+        import torch
+        self._expect(st["Y"], (self.M, self.F, self.J), torch.complex64, cuda=True)
+        self._expect(st["W"], (self.F, self.M, self.M), torch.complex64, cuda=True)
+        self._expect(st["T"], (self.N, self.F, self.B), torch.float32, cuda=True)
+        self._expect(st["V"], (self.N, self.B, self.J), torch.float32, cuda=True)
+        self._expect(st["logdet"], (self.F,), torch.float64, cuda=True)
+        _check(lib().ctfmnmf_set_state(self._h, _ptr(st["Y"]), _ptr(st["W"]), _ptr(st["T"]), _ptr(st["V"]),
+                                       _ptr(st["logdet"])), self._h)
 
     # -- outputs
     def cost(self) -> float:

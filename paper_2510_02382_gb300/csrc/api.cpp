@@ -414,6 +414,30 @@ int ctfmnmf_load_stft_host(ctfmnmf_t h, const void* X)
     return ctfmnmf_load_stft(h, h->d.staging);
 }
 
+int ctfmnmf_set_state(ctfmnmf_t h, const void* Y, const void* W, const float* T, const float* V,
+                      const double* logdet)
+{
+    if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
+    if (!Y || !W || !T || !V || !logdet) return fail(h, CTFMNMF_EINVAL, "null pointer argument");
+    if (h->d.X && !h->loaded) return fail(h, CTFMNMF_ESTATE, "the IP update needs ctfmnmf_load_stft first");
+    h->err[0] = 0;
+    h->loaded = false;
+    const Shape& s = h->s;
+    // the rows in the loaded layout (as ctfmnmf_load_stft does with X; it also resets W,
+    // log|det| and the pending scale), then W, log|det| and the factors over them
+    CUDA_TRY(h, ctf::launch_load(s, h->d, (const float2*)Y, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.W, W, sizeof(float2) * (size_t)s.F * s.M * s.M, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.logdet, logdet, sizeof(double) * s.F, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(h, ctf::launch_init_nmf(s, h->d, T, V, 0, h->stream));
+    CUDA_TRY(h, ctf::launch_psd(s, h->d, h->stream));
+    h->launches += 3;
+    int rc = check_flag(h, 3, "the state");
+    if (rc != CTFMNMF_OK) return rc;
+    h->loaded = true;
+    return CTFMNMF_OK;
+}
+
 int ctfmnmf_set_init(ctfmnmf_t h, const float* T0, const float* V0)
 {
     if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
@@ -427,6 +451,7 @@ int ctfmnmf_set_init(ctfmnmf_t h, const float* T0, const float* V0)
 
 int ctfmnmf_iterate(ctfmnmf_t h, int n_iter)
 {
+    ctf::TraceRange trace("ctfmnmf_iterate");
     if (!h) return fail(nullptr, CTFMNMF_EINVAL, "handle is NULL");
     if (n_iter < 0) return fail(h, CTFMNMF_EINVAL, "n_iter=%d is negative", n_iter);
     if (!h->loaded) return fail(h, CTFMNMF_ESTATE, "no STFT loaded");

@@ -355,6 +355,7 @@ int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* o
 
 int ctfmnmf_batch_iterate(ctfmnmf_batch_t b, int n_iter)
 {
+    ctf::TraceRange trace("ctfmnmf_batch_iterate");
     ctf::set_thread_error("");
     if (!b) return fail_b(CTFMNMF_EINVAL, "batch is NULL");
     if (n_iter < 0) return fail_b(CTFMNMF_EINVAL, "n_iter is negative");
@@ -422,6 +423,63 @@ int ctfmnmf_batch_info(ctfmnmf_batch_t b, int* info)
     info[2] = (int)b->plan.frames.size();
     info[3] = b->policy;
     info[4] = (int)(b->launches & 0x7fffffff);
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_batch_load_stft(ctfmnmf_batch_t b, const void* X, const long long* offsets)
+{
+    ctf::set_thread_error("");
+    if (!b || !X || !offsets) return fail_b(CTFMNMF_EINVAL, "need a batch, a buffer and offsets");
+    cudaStream_t st = b->hs[0]->stream;
+    for (size_t k = 0; k < b->hs.size(); ++k) {
+        ctfmnmf* h = b->hs[k];
+        h->loaded = false;
+        if (offsets[k] < 0) return fail_b(CTFMNMF_EINVAL, "negative offset");
+        const float2* Xk = static_cast<const float2*>(X) + offsets[k];
+        if (cudaMemsetAsync(h->d.flag, 0, sizeof(int) * 2, st) != cudaSuccess ||
+            ctf::launch_load(h->s, h->d, Xk, st) != cudaSuccess)
+            return fail_b(CTFMNMF_ECUDA, "loading a mixture failed");
+        if (h->d.X &&
+            cudaMemcpyAsync(h->d.X, h->d.Y, sizeof(float2) * (size_t)h->s.F * h->s.M * h->s.Jp,
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return fail_b(CTFMNMF_ECUDA, "keeping the observation failed");
+        h->launches += 1;
+    }
+    std::vector<int> flags(b->hs.size(), 0);
+    for (size_t k = 0; k < b->hs.size(); ++k)
+        if (cudaMemcpyAsync(&flags[k], b->hs[k]->d.flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail_b(CTFMNMF_ECUDA, "reading the input checks failed");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail_b(CTFMNMF_ECUDA, "loading the batch failed");
+    for (size_t k = 0; k < b->hs.size(); ++k) {
+        if (flags[k] & 1) {
+            cudaMemsetAsync(b->hs[k]->d.flag, 0, sizeof(int), st);
+            return fail_b(CTFMNMF_ENONFINITE, "a mixture's X holds NaN or Inf");
+        }
+    }
+    for (ctfmnmf* h : b->hs) h->loaded = true;
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_batch_set_init(ctfmnmf_batch_t b, const float* T0, const long long* t_offsets, const float* V0,
+                           const long long* v_offsets)
+{
+    ctf::set_thread_error("");
+    if (!b || (T0 && !t_offsets) || (V0 && !v_offsets)) return fail_b(CTFMNMF_EINVAL, "need a batch and offsets");
+    for (size_t k = 0; k < b->hs.size(); ++k) {
+        const int rc = ctfmnmf_set_init(b->hs[k], T0 ? T0 + t_offsets[k] : nullptr, V0 ? V0 + v_offsets[k] : nullptr);
+        if (rc != CTFMNMF_OK) return fail_b(rc, "%s", ctfmnmf_last_error(b->hs[k]));
+    }
+    return CTFMNMF_OK;
+}
+
+int ctfmnmf_batch_get_separated(ctfmnmf_batch_t b, void* C, const long long* offsets)
+{
+    ctf::set_thread_error("");
+    if (!b || !C || !offsets) return fail_b(CTFMNMF_EINVAL, "need a batch, a buffer and offsets");
+    for (size_t k = 0; k < b->hs.size(); ++k) {
+        const int rc = ctfmnmf_get_separated(b->hs[k], static_cast<float2*>(C) + offsets[k]);
+        if (rc != CTFMNMF_OK) return fail_b(rc, "%s", ctfmnmf_last_error(b->hs[k]));
+    }
     return CTFMNMF_OK;
 }
 

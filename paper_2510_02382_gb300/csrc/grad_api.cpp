@@ -224,6 +224,7 @@ int ctfmnmf_grad_set_stream(ctfmnmf_grad_t g, void* stream)
 
 int ctfmnmf_grad_forward(ctfmnmf_grad_t g, const void* X, const float* T0, const float* V0, void* C)
 {
+    ctf::TraceRange trace("ctfmnmf_grad_forward");
     ctf::set_thread_error("");
     if (!g) return gfail(CTFMNMF_EINVAL, "object is NULL");
     if (!X || !T0 || !V0 || !C) return gfail(CTFMNMF_EINVAL, "null pointer argument");
@@ -273,6 +274,7 @@ int ctfmnmf_grad_forward(ctfmnmf_grad_t g, const void* X, const float* T0, const
 
 int ctfmnmf_grad_backward(ctfmnmf_grad_t g, const void* gC, void* gX, float* gT0, float* gV0)
 {
+    ctf::TraceRange trace("ctfmnmf_grad_backward");
     ctf::set_thread_error("");
     if (!g) return gfail(CTFMNMF_EINVAL, "object is NULL");
     if (!gC || !gX || !gT0 || !gV0) return gfail(CTFMNMF_EINVAL, "null pointer argument");

@@ -31,7 +31,18 @@ struct ctfmnmf {
     char err[256];
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace ctf {
+// An NVTX range over a host call (visible in Nsight timelines; costs nothing when no tool
+// is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
 // kernels enqueued by one ctfmnmf_iterate of n_iter iterations on the two-kernel path
 long long iteration_kernels(int n_iter);
 // finalize kernels (pending normalisation) launched at the end of every iterate call

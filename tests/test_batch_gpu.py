@@ -104,3 +104,40 @@ def test_batched_workload_sampled_mixtures():
     batch.close()
     for s in solvers:
         s.close()
+
+
+def test_batch_ragged_buffers_match_per_handle_calls():
+    """ctfmnmf_batch_load_stft / _set_init / _get_separated over one concatenated buffer
+    with offsets give exactly what the per-handle calls give."""
+    import torch
+    from paper_2510_02382_gb300.api import Batch
+    mixes = [synth.random_case(700 + k, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+             for k, (M, N, Ln, F, J, B) in enumerate(RAGGED[:4])]
+    # per-handle reference
+    ref_solvers = _loaded(mixes)
+    ref_batch = Batch(ref_solvers)
+    ref_batch.iterate(3)
+    ref = [s.get_separated().cpu().numpy() for s in ref_solvers]
+    ref_batch.close()
+    # the same through ragged buffers
+    solvers = [make_solver(m, path="two_kernel") for m in mixes]
+    batch = Batch(solvers)
+    X = torch.from_numpy(np.concatenate([m.X.ravel() for m in mixes])).cuda()
+    T0 = torch.from_numpy(np.concatenate([m.T0.ravel() for m in mixes])).cuda()
+    V0 = torch.from_numpy(np.concatenate([m.V0.ravel() for m in mixes])).cuda()
+    xo = np.cumsum([0] + [m.X.size for m in mixes])[:-1]
+    to = np.cumsum([0] + [m.T0.size for m in mixes])[:-1]
+    vo = np.cumsum([0] + [m.V0.size for m in mixes])[:-1]
+    co = np.cumsum([0] + [m.images.size for m in mixes])
+    batch.load_stft(X, xo)
+    batch.set_init(T0, to, V0, vo)
+    batch.iterate(3)
+    C = torch.empty(int(co[-1]), dtype=torch.complex64, device="cuda")
+    batch.get_separated(C, co[:-1])
+    torch.cuda.synchronize()
+    Cn = C.cpu().numpy()
+    for k, m in enumerate(mixes):
+        assert np.array_equal(Cn[co[k]:co[k + 1]].reshape(m.images.shape), ref[k]), k
+    batch.close()
+    for s in solvers + ref_solvers:
+        s.close()

@@ -317,3 +317,43 @@ def test_every_bin_phase_shape_matches_oracle(fpt):
     ok, err = cost_close(s.cost(), ref["cost"], 1e-5, sp.F, sp.J, sp.M)
     assert ok, err
     s.close()
+
+
+def test_checkpoint_resume_continues():
+    """Export the state after 7 iterations, restore it into a fresh handle, run 5 more on
+    both: the same results to FP32 rounding (the restored handle forms 1/lambda from the
+    exported T and V, the exporting one kept the frame phase's), and both track the
+    oracle's 12 iterations."""
+    import torch
+    from paper_2510_02382_gb300.api import CtfMnmfError
+    mix = synth.random_case(61, M=3, N=2, F=9, J=150, B=5, Ln=(2, 1))
+    sp = mix.spec
+    a = make_solver(mix, path="two_kernel")
+    a.load_stft(torch.from_numpy(mix.X).cuda())
+    a.set_init(torch.from_numpy(mix.T0).cuda(), torch.from_numpy(mix.V0).cuda())
+    a.iterate(7)
+    st = {k: v.clone() for k, v in a.get_state().items()}
+    b = make_solver(mix, path="two_kernel")
+    b.set_state(st)
+    a.iterate(5)
+    b.iterate(5)
+    ya, yb = a.get_demixed().cpu().numpy(), b.get_demixed().cpu().numpy()
+    assert rel_fro(yb, ya) < 1e-5
+    ok, err = cost_close(b.cost(), a.cost(), 1e-6, sp.F, sp.J, sp.M)
+    assert ok, err
+    ref = run_oracle(mix, 12)
+    assert rel_fro(yb, ref["y"]) < 1e-4
+    ok, err = cost_close(b.cost(), ref["cost"], 1e-5, sp.F, sp.J, sp.M)
+    assert ok, err
+    bad = dict(st)
+    bad["Y"] = st["Y"].clone()
+    bad["Y"][0, 0, 0] = float("nan")
+    with pytest.raises(CtfMnmfError) as e:
+        b.set_state(bad)
+    assert e.value.name == "ENONFINITE"
+    ip = make_solver(mix, path="two_kernel", w_update="ip")
+    with pytest.raises(CtfMnmfError) as e:
+        ip.set_state(st)
+    assert e.value.name == "ESTATE"
+    for h in (a, b, ip):
+        h.close()
