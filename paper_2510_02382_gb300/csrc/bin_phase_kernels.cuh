@@ -119,9 +119,11 @@ inline cudaError_t launch_m(const Shape& s, const State& d, int v_tap0, int fpt,
 template <int M, int FPT>
 inline cudaError_t launch_ip_mf(const Shape& s, const State& d, int v_tap0, int nt, cudaStream_t st, bool cfg)
 {
-    // one block per SM guaranteed: the covariance sums and the FP64 solve need registers
+    // the covariance sums hold M (M + 1) / 2 complex partials per frame and the FP64 solve
+    // runs on warp 0 with a few doubles per lane: 80 registers (three 256-thread blocks per
+    // SM) below 8 frames per thread
     constexpr int kMaxT = FPT == 8 ? 512 : 256;
-    constexpr int kMinB = 1;
+    constexpr int kMinB = FPT == 8 ? 1 : 3;
     if (cfg) {
         int dev = 0, optin = 0;
         cudaError_t e = cudaGetDevice(&dev);

@@ -14,17 +14,20 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 // Sum a[V] over the thread block; every thread finds the sums in out[V] (shared) afterwards.
-// red holds (threads / 32) * V floats.
+// red holds (threads / 32) * V floats. The warp stage is a reduce-scatter over the next
+// power of two of V values (V - 1 + log2(32 / VP) exchanges instead of 5 V).
 template <int V>
 __device__ __forceinline__ void block_sum(float (&a)[V], float* red, float* out)
 {
+    constexpr int VP = pow2_at_least(V);
+    static_assert(VP <= 32, "block_sum reduces at most 32 values");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float b[VP];
 #pragma unroll
-    for (int v = 0; v < V; ++v) a[v] = warp_sum(a[v]);
-    if (lane == 0) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) red[warp * V + v] = a[v];
-    }
+    for (int v = 0; v < VP; ++v) b[v] = v < V ? a[v] : 0.f;
+    reduce_scatter<VP>(b, lane);
+    constexpr int per = 32 / VP;                  // lanes holding each value's sum
+    if ((lane & (per - 1)) == 0 && lane / per < V) red[warp * V + lane / per] = b[0];
     __syncthreads();
     if ((int)threadIdx.x < V) {
         float t = 0.f;

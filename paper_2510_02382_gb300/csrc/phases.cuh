@@ -70,170 +70,126 @@ __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
     return b;
 }
 
-// Complex FP64 helpers of the IP sweep. Every index below is a compile-time constant once
-// the loops over M are unrolled, so the small matrices live in registers; partial pivoting
-// swaps a candidate row into place whenever it is larger (the row of largest magnitude ends
-// up as the pivot, the first one on ties).
-template <int M, int C>
-__device__ __forceinline__ void pivot_rows(double (&ar)[M][C], double (&ai)[M][C], int c)
-{
-#pragma unroll
-    for (int p = 0; p < M; ++p) {
-        if (p <= c) continue;
-        const double mc = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
-        const double mp = ar[p][c] * ar[p][c] + ai[p][c] * ai[p][c];
-        const bool sw = mp > mc;
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            const double xr = ar[c][q], xi = ai[c][q];
-            ar[c][q] = sw ? ar[p][q] : xr;
-            ai[c][q] = sw ? ai[p][q] : xi;
-            ar[p][q] = sw ? xr : ar[p][q];
-            ai[p][q] = sw ? xi : ai[p][q];
-        }
-    }
-}
-
-// Forward elimination below pivot c (columns c..C-1); false if the pivot is zero.
-template <int M, int C>
-__device__ __forceinline__ bool eliminate(double (&ar)[M][C], double (&ai)[M][C], int c)
-{
-    const double m2 = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
-    if (!(m2 > 0.0)) return false;
-    const double ir = ar[c][c] / m2, ii = -ai[c][c] / m2;      // 1 / pivot
-#pragma unroll
-    for (int p = 0; p < M; ++p) {
-        if (p <= c) continue;
-        const double fr = ar[p][c] * ir - ai[p][c] * ii, fi = ar[p][c] * ii + ai[p][c] * ir;
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            if (q < c) continue;
-            ar[p][q] -= fr * ar[c][q] - fi * ai[c][q];
-            ai[p][q] -= fr * ai[c][q] + fi * ar[c][q];
-        }
-    }
-    return true;
-}
-
-// |det A| of a small complex matrix by Gaussian elimination (A is overwritten).
+// Entry (a, b) of the Hermitian Q_r stored as M real diagonal entries, then (re, im) of
+// Q_r[a][b] for a < b in row-major pair order.
 template <int M>
-__device__ __forceinline__ double abs_det(double (&ar)[M][M], double (&ai)[M][M])
+__device__ __forceinline__ void q_entry(const float* Qr, int a, int b, double& re, double& im)
 {
-    double det = 1.0;
-#pragma unroll
-    for (int c = 0; c < M; ++c) {
-        pivot_rows<M, M>(ar, ai, c);
-        if (!eliminate<M, M>(ar, ai, c)) return 0.0;
-        det *= sqrt(ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c]);
+    if (a == b) {
+        re = Qr[a];
+        im = 0.0;
+        return;
     }
-    return det;
+    const int lo = min(a, b), hi = max(a, b);
+    const int pq = lo * M - lo * (lo + 1) / 2 + (hi - lo - 1);
+    re = Qr[M + 2 * pq];
+    im = a < b ? (double)Qr[M + 2 * pq + 1] : -(double)Qr[M + 2 * pq + 1];
 }
 
-// The IP sweep of Eqs. 9-10 for one bin, by one thread in FP64: for r = 0..M-1 in order,
-// solve (W Q_r) w = e_r, scale w by (w^H Q_r w)^{-1/2}, set row r of W to w^H.
-// Qs[r][.] holds Q_r as M real diagonal entries, then (re, im) of Q_r[a][b] for a < b in
-// row-major pair order; W (M x M, row r = w_r^H) is updated in place. A singular W Q_r (a
-// bin without energy, or a covariance that FP32 left without full rank) leaves that row
-// unchanged. Returns |det W_new| / |det W_old|.
+// The IP sweep of Eqs. 9-10 for one bin, in FP64 by one warp (all 32 lanes call it): for
+// r = 0..M-1 in order, solve (W Q_r) x = e_r, scale by s = (x^H Q_r x)^{-1/2}, set row r of
+// W to s x^H. Lane p (M + 1) + q holds entry (p, q) of the augmented matrix [W Q_r | e_r]
+// (and W[p][q] for q < M); Gauss-Jordan elimination with partial pivoting (the row of
+// largest |a|^2 in the column, the first on ties, swapped with the pivot row) leaves x in
+// column M. Qs[r][.] holds Q_r (see q_entry); W (M x M floats, row r = w_r^H) is updated in
+// place. A singular W Q_r (a bin without energy, or a covariance that FP32 left without
+// full rank) or x^H Q_r x <= 0 leaves that row unchanged.
+// *ratio_out = |det W_new| / |det W_old|, without a determinant: replacing row r of W by
+// s x^H is the rank-one update W + e_r d^H, and by the matrix determinant lemma
+// det W_new / det W = 1 + d^H W^{-1} e_r = s x^H Q_r x (W^{-1} e_r = Q_r x), so each applied
+// row contributes the real factor (x^H Q_r x)^{1/2}.
 template <int M>
-__device__ __forceinline__ double ip_solve(const float* Qs, float2* W)
+__device__ __forceinline__ void ip_solve_warp(const float* Qs, float2* W, float* ratio_out, const int lane)
 {
-    constexpr int NQ = M * M;
-    double wr[M][M], wi[M][M], tr[M][M], ti[M][M];
-#pragma unroll
-    for (int p = 0; p < M; ++p)
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            wr[p][c] = tr[p][c] = W[p * M + c].x;
-            wi[p][c] = ti[p][c] = W[p * M + c].y;
-        }
-    const double det_old = abs_det<M>(tr, ti);
+    constexpr int NQ = M * M, C = M + 1;
+    static_assert(M * C <= 32, "one lane per entry of the augmented matrix");
+    const unsigned full = 0xffffffffu;
+    const int p = lane / C, q = lane - p * C;
+    const bool wl = p < M && q < M;                 // lanes holding W[p][q]
+    auto at = [](int row, int col) { return min(row * C + col, 31); };
+    double wre = 0.0, wim = 0.0;
+    if (wl) {
+        const float2 w = W[p * M + q];
+        wre = w.x;
+        wim = w.y;
+    }
+    double ratio = 1.0;
 #pragma unroll
     for (int r = 0; r < M; ++r) {
-        double qr[M][M], qi[M][M];
+        const float* Qr = Qs + r * NQ;
+        // A[p][q] = sum_k W[p][k] Q_r[k][q]; column M is e_r
+        double ar = 0.0, ai = 0.0;
 #pragma unroll
-        for (int a = 0; a < M; ++a) {
-            qr[a][a] = Qs[r * NQ + a];
-            qi[a][a] = 0.0;
+        for (int k = 0; k < M; ++k) {
+            const double wkr = __shfl_sync(full, wre, at(p, k)), wki = __shfl_sync(full, wim, at(p, k));
+            double qr = 0.0, qi = 0.0;
+            if (wl) q_entry<M>(Qr, k, q, qr, qi);
+            ar += wkr * qr - wki * qi;
+            ai += wkr * qi + wki * qr;
         }
-        {
-            int pq = 0;
-#pragma unroll
-            for (int a = 0; a < M; ++a)
-#pragma unroll
-                for (int b = 0; b < M; ++b) {
-                    if (b <= a) continue;
-                    qr[a][b] = Qs[r * NQ + M + 2 * pq];
-                    qi[a][b] = Qs[r * NQ + M + 2 * pq + 1];
-                    qr[b][a] = qr[a][b];
-                    qi[b][a] = -qi[a][b];
-                    ++pq;
-                }
-        }
-        double ar[M][M + 1], ai[M][M + 1];               // [W Q_r | e_r]
-#pragma unroll
-        for (int p = 0; p < M; ++p) {
-#pragma unroll
-            for (int c = 0; c < M; ++c) {
-                double sr = 0.0, si = 0.0;
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    sr += wr[p][k] * qr[k][c] - wi[p][k] * qi[k][c];
-                    si += wr[p][k] * qi[k][c] + wi[p][k] * qr[k][c];
-                }
-                ar[p][c] = sr;
-                ai[p][c] = si;
-            }
-            ar[p][M] = p == r ? 1.0 : 0.0;
-            ai[p][M] = 0.0;
+        if (q == M) {
+            ar = p == r ? 1.0 : 0.0;
+            ai = 0.0;
         }
         bool ok = true;
 #pragma unroll
         for (int c = 0; c < M; ++c) {
-            pivot_rows<M, M + 1>(ar, ai, c);
-            ok = ok && eliminate<M, M + 1>(ar, ai, c);
+            const double mag = ar * ar + ai * ai;
+            int piv = c;
+            double best = __shfl_sync(full, mag, at(c, c));
+#pragma unroll
+            for (int pp = c + 1; pp < M; ++pp) {
+                const double m = __shfl_sync(full, mag, at(pp, c));
+                if (m > best) {
+                    best = m;
+                    piv = pp;
+                }
+            }
+            if (!(best > 0.0)) {                    // the same decision on every lane
+                ok = false;
+                break;
+            }
+            const int src = p == c ? piv : (p == piv ? c : p);
+            const double sr = __shfl_sync(full, ar, at(src, q)), si = __shfl_sync(full, ai, at(src, q));
+            ar = sr;
+            ai = si;
+            const double pr = __shfl_sync(full, ar, at(c, c)), pim = __shfl_sync(full, ai, at(c, c));
+            const double im2 = 1.0 / best;
+            const double ir = pr * im2, ii = -pim * im2;          // 1 / pivot
+            const double cr = __shfl_sync(full, ar, at(c, q)), ci = __shfl_sync(full, ai, at(c, q));
+            const double fr = __shfl_sync(full, ar, at(p, c)), fi = __shfl_sync(full, ai, at(p, c));
+            const double nr = cr * ir - ci * ii, ni = cr * ii + ci * ir;   // pivot row, scaled
+            if (p == c) {
+                ar = nr;
+                ai = ni;
+            } else {
+                ar -= fr * nr - fi * ni;
+                ai -= fr * ni + fi * nr;
+            }
         }
         if (!ok) continue;
-        double xr[M], xi[M];                             // back substitution
-#pragma unroll
-        for (int p = M - 1; p >= 0; --p) {
-            double sr = ar[p][M], si = ai[p][M];
-#pragma unroll
-            for (int q = 0; q < M; ++q) {
-                if (q <= p) continue;
-                sr -= ar[p][q] * xr[q] - ai[p][q] * xi[q];
-                si -= ar[p][q] * xi[q] + ai[p][q] * xr[q];
-            }
-            const double den = ar[p][p] * ar[p][p] + ai[p][p] * ai[p][p];
-            xr[p] = (sr * ar[p][p] + si * ai[p][p]) / den;
-            xi[p] = (si * ar[p][p] - sr * ai[p][p]) / den;
+        // x^H Q_r x: lane (a, b) adds conj(x_a) Q_r[a][b] x_b
+        const double xbr = __shfl_sync(full, ar, at(q, M)), xbi = __shfl_sync(full, ai, at(q, M));
+        const double xar = __shfl_sync(full, ar, at(p, M)), xai = __shfl_sync(full, ai, at(p, M));
+        double term = 0.0;
+        if (wl) {
+            double qr, qi;
+            q_entry<M>(Qr, p, q, qr, qi);
+            const double ur = qr * xbr - qi * xbi, ui = qr * xbi + qi * xbr;
+            term = xar * ur + xai * ui;
         }
-        double nrm = 0.0;                                // w^H Q_r w (real)
 #pragma unroll
-        for (int a = 0; a < M; ++a)
-#pragma unroll
-            for (int b = 0; b < M; ++b) {
-                const double ur = qr[a][b] * xr[b] - qi[a][b] * xi[b], ui = qr[a][b] * xi[b] + qi[a][b] * xr[b];
-                nrm += xr[a] * ur + xi[a] * ui;
-            }
-        if (!(nrm > 0.0)) continue;
-        const double sc = 1.0 / sqrt(nrm);
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            wr[r][c] = xr[c] * sc;
-            wi[r][c] = -xi[c] * sc;                      // row r = w^H
+        for (int o = 16; o >= 1; o >>= 1) term += __shfl_xor_sync(full, term, o);
+        if (!(term > 0.0)) continue;                // the same sum on every lane
+        const double sc = rsqrt(term);
+        ratio *= term * sc;
+        if (wl && p == r) {                         // row r = s x^H
+            wre = xbr * sc;
+            wim = -xbi * sc;
         }
     }
-#pragma unroll
-    for (int p = 0; p < M; ++p)
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            W[p * M + c] = make_float2((float)wr[p][c], (float)wi[p][c]);
-            tr[p][c] = wr[p][c];
-            ti[p][c] = wi[p][c];
-        }
-    const double det_new = abs_det<M>(tr, ti);
-    return det_old > 0.0 ? det_new / det_old : 1.0;
+    if (wl) W[p * M + q] = make_float2((float)wre, (float)wim);
+    if (lane == 0) *ratio_out = (float)ratio;
 }
 
 // One CTF-MNMF-ISS bin update (Sec. III) for bin i by group g.
@@ -246,7 +202,7 @@ __device__ __forceinline__ double ip_solve(const float* Qs, float2* W)
 //        mupart[i][r] = sum_j |y_r(j)|^2;
 //        returns prod_r (1 - z_r), the factor of |det W_i| (Eq. 13).
 // IP = true replaces the ISS sweep by the IP update of Eqs. 9-10 (M <= 4): the weighted
-// covariances Q_r (Eq. 8) of the kept observation d.X, the sequential solves (ip_solve),
+// covariances Q_r (Eq. 8) of the kept observation d.X, the sequential solves (ip_solve_warp),
 // then y = W x; the return value is then |det W_new| / |det W_old|.
 template <int M, int FPT, bool GLOBAL, int KB = 16, bool IP = false>
 __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const int i, const Grp& g,
@@ -355,7 +311,7 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
             }
         }
         grp_sync(g);
-        if (g.tid == 0) Qs[M * NQ] = (float)ip_solve<M>(Qs, Wm);   // the slot after Q is free
+        if (g.tid < 32) ip_solve_warp<M>(Qs, Wm, Qs + M * NQ, lane);   // the slot after Q is free
         grp_sync(g);
         detf = Qs[M * NQ];
 #pragma unroll
