@@ -271,6 +271,29 @@ def test_ip_last_row_satisfies_head():
         assert np.max(np.abs(W2[i] @ Q[r, i] @ w - np.eye(M)[r])) < 1e-10
 
 
+def test_ip_row_update_determinant_factor():
+    """Each IP row update (Eqs. 9-10) multiplies |det W| by (x^H Q_r x)^{1/2}, where
+    x = (W Q_r)^{-1} e_r is taken before the update: replacing row r is the rank-one update
+    W + e_r d^H, and the matrix determinant lemma with W^{-1} e_r = Q_r x gives the factor.
+    The IP bin kernel returns |det W_new| / |det W_old| in this form; here the oracle's sweep
+    is checked against it with determinants from slogdet. Step r changes row r only, so the
+    matrix before step r is the swept rows 0..r-1 over the initial rows r..M-1."""
+    rng = np.random.default_rng(23)
+    for M in (2, 3, 4):
+        I = 3
+        W = _rand_W(rng, M, I)
+        Q = np.stack([np.stack([_rand_hpd(rng, M) for _ in range(I)]) for _ in range(M)])
+        W2 = O.ip_sweep(W, Q)
+        expect = np.zeros(I)
+        for r in range(M):
+            Wb = np.concatenate([W2[:, :r], W[:, r:]], axis=1)
+            for i in range(I):
+                x = np.linalg.solve(Wb[i] @ Q[r, i], np.eye(M)[r])
+                expect[i] += 0.5 * np.log((x.conj() @ Q[r, i] @ x).real)
+        got = np.linalg.slogdet(W2)[1] - np.linalg.slogdet(W)[1]
+        assert np.max(np.abs(got - expect)) < 1e-10, (M, got, expect)
+
+
 def _head_residual(W, Q):
     M = W.shape[1]
     res = 0.0
