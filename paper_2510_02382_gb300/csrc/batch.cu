@@ -28,7 +28,8 @@ cudaError_t batch_bin_m8(int fpt, int kb, const MixDesc* mixes, const int2* work
 constexpr int kBatchFrameThreads = 256;
 constexpr int kBatchFrameSmemBytes = 48 * 1024;
 
-template <int BB>
+// EXACT: every mixture of the launch has B equal to the class width BB.
+template <int BB, bool EXACT>
 __global__ void __launch_bounds__(kBatchFrameThreads)
 batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ work, const int v_tap0,
                    const int normalize)
@@ -50,8 +51,10 @@ batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ w
     const int fixed = frame_smem_fixed<BB>(kBatchFrameThreads);
     const int FC = frame_chunk(kBatchFrameSmemBytes / 4, s.B, fixed);
     const ScaleJob job{s_scale, red_cta, normalize};
-    if constexpr (BB <= 16) frame_item<BB>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
-    else frame_item_wide<BB>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+    if constexpr (BB <= 16)
+        frame_item<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+    else
+        frame_item_wide<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
     if (w.y == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
 }
 
@@ -72,14 +75,23 @@ cudaError_t launch_batch_bin(const BatchClass& c, const MixDesc* mixes, int v_ta
 
 static int batch_frame_bb(int B) { return B <= 4 ? 4 : B <= 8 ? 8 : B <= 10 ? 10 : B <= 16 ? 16 : 32; }
 
+template <int BB>
+static cudaError_t batch_frame_set(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_frame_kernel<BB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_frame_kernel<BB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 cudaError_t configure_batch_frame()
 {
     const int bytes = kBatchFrameSmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(batch_frame_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_frame_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_frame_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_frame_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_frame_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = batch_frame_set<4>(bytes);
+    if (e == cudaSuccess) e = batch_frame_set<8>(bytes);
+    if (e == cudaSuccess) e = batch_frame_set<10>(bytes);
+    if (e == cudaSuccess) e = batch_frame_set<16>(bytes);
+    if (e == cudaSuccess) e = batch_frame_set<32>(bytes);
     return e;
 }
 
@@ -95,16 +107,25 @@ int batch_frame_chunk(int B, int BB)
     return frame_chunk(kBatchFrameSmemBytes / 4, B, fixed);
 }
 
-cudaError_t launch_batch_frame(int BB, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
+template <int BB>
+static void batch_frame_launch(bool exact, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
+                               int normalize, size_t smem, cudaStream_t st)
+{
+    if (exact) batch_frame_kernel<BB, true><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize);
+    else batch_frame_kernel<BB, false><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize);
+}
+
+cudaError_t launch_batch_frame(int BB, int exact, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
                                int normalize, cudaStream_t st)
 {
     const size_t smem = kBatchFrameSmemBytes;
+    const bool ex = exact != 0;
     switch (BB) {
-        case 4: batch_frame_kernel<4><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize); break;
-        case 8: batch_frame_kernel<8><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize); break;
-        case 10: batch_frame_kernel<10><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize); break;
-        case 16: batch_frame_kernel<16><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize); break;
-        case 32: batch_frame_kernel<32><<<blocks, kBatchFrameThreads, smem, st>>>(mixes, work, v_tap0, normalize); break;
+        case 4: batch_frame_launch<4>(ex, mixes, work, blocks, v_tap0, normalize, smem, st); break;
+        case 8: batch_frame_launch<8>(ex, mixes, work, blocks, v_tap0, normalize, smem, st); break;
+        case 10: batch_frame_launch<10>(ex, mixes, work, blocks, v_tap0, normalize, smem, st); break;
+        case 16: batch_frame_launch<16>(ex, mixes, work, blocks, v_tap0, normalize, smem, st); break;
+        case 32: batch_frame_launch<32>(ex, mixes, work, blocks, v_tap0, normalize, smem, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

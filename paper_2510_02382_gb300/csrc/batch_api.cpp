@@ -26,7 +26,7 @@ using ctf::MixDesc;
 namespace {
 
 struct FrameClass {
-    int BB, blocks;
+    int BB, exact, blocks;       // exact: every mixture of the class has B == BB
     int2* work;
 };
 
@@ -104,11 +104,13 @@ int make_plan(const std::vector<ctfmnmf*>& hs, int pref, bool merge, Plan* out)
         const int BB = ctf::batch_frame_class(s.B);
         if (ctf::batch_frame_chunk(s.B, BB) < 4) return CTFMNMF_EUNSUPPORTED;
         const int items = (s.Jp / 8) * s.N;
-        for (int it = 0; it < items; ++it) fwork[BB].push_back(make_int2((int)b, it));
+        const int key = 2 * BB + (s.B == BB ? 1 : 0);     // mixtures whose B is the class width apart
+        for (int it = 0; it < items; ++it) fwork[key].push_back(make_int2((int)b, it));
     }
     for (auto& kv : fwork) {
         FrameClass f;
-        f.BB = kv.first;
+        f.BB = kv.first / 2;
+        f.exact = kv.first & 1;
         f.blocks = (int)kv.second.size();
         f.work = nullptr;
         if (cudaMalloc((void**)&f.work, sizeof(int2) * kv.second.size()) != cudaSuccess ||
@@ -184,7 +186,7 @@ cudaError_t enqueue_batch(ctfmnmf_batch* b, const Plan& p, int n_iter, cudaStrea
             }
         }
         for (const auto& f : p.frames) {
-            cudaError_t e = ctf::launch_batch_frame(f.BB, b->dmix, f.work, f.blocks, b->v_tap0, b->normalize, st);
+            cudaError_t e = ctf::launch_batch_frame(f.BB, f.exact, b->dmix, f.work, f.blocks, b->v_tap0, b->normalize, st);
             if (e != cudaSuccess) return e;
         }
     }

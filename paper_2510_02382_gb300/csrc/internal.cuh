@@ -116,7 +116,7 @@ int bases_class(int B);   // 4, 8, 10 or 16: the basis-MU pass width for B bases
 cudaError_t configure_batch_frame();
 int batch_frame_class(int B);
 int batch_frame_chunk(int B, int BB);
-cudaError_t launch_batch_frame(int BB, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
+cudaError_t launch_batch_frame(int BB, int exact, const MixDesc* mixes, const int2* work, int blocks, int v_tap0,
                                int normalize, cudaStream_t st);
 
 // Long-J bin phase (cluster_bin.cu): one bin over a cluster of cl blocks of nt threads,

@@ -171,7 +171,8 @@ cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st)
 constexpr int kFrameThreads = 256;
 constexpr int kFrameSmemBytes = 48 * 1024;
 
-template <int BB>
+// EXACT: s.B equals the class width BB (the per-basis bounds tests fold away).
+template <int BB, bool EXACT>
 __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape s, const State d,
                                                                     const int v_tap0, const int normalize,
                                                                     const int FC)
@@ -181,8 +182,10 @@ __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape 
     __shared__ float red_cta[(kFrameThreads / 32) * CTFMNMF_MAX_M];
     const Grp g{(int)threadIdx.x, kFrameThreads, 0};
     const ScaleJob job{s_scale, red_cta, normalize};     // formed while the item's staging is in flight
-    if constexpr (BB <= 16) frame_item<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
-    else frame_item_wide<BB>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+    if constexpr (BB <= 16)
+        frame_item<BB, EXACT>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+    else
+        frame_item_wide<BB, EXACT>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
     if (blockIdx.x == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
 }
 
@@ -197,20 +200,33 @@ static int frame_fc(const Shape& s, int BB)
 
 static int frame_bb(int B) { return B <= 4 ? 4 : B <= 8 ? 8 : B <= 10 ? 10 : B <= 16 ? 16 : 32; }
 
+template <int BB>
+static cudaError_t frame_bb_set(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(frame_phase_kernel<BB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(frame_phase_kernel<BB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 // Allow the frame-phase kernels more than 48 KB of shared memory (dynamic + static).
 cudaError_t configure_frame_phase()
 {
     const int bytes = kFrameSmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(frame_phase_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(frame_phase_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(frame_phase_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(frame_phase_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(frame_phase_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = frame_bb_set<4>(bytes);
+    if (e == cudaSuccess) e = frame_bb_set<8>(bytes);
+    if (e == cudaSuccess) e = frame_bb_set<10>(bytes);
+    if (e == cudaSuccess) e = frame_bb_set<16>(bytes);
+    if (e == cudaSuccess) e = frame_bb_set<32>(bytes);
     return e;
+}
+
+template <int BB>
+static void frame_launch(const Shape& s, const State& d, int v_tap0, int normalize, int FC, int items, size_t smem,
+                         cudaStream_t st)
+{
+    if (s.B == BB) frame_phase_kernel<BB, true><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC);
+    else frame_phase_kernel<BB, false><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC);
 }
 
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
@@ -222,11 +238,11 @@ cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int n
     if (FC < 4 || (FC * s.B) % 4 != 0 || s.Jp % kFrameTile != 0) return cudaErrorInvalidValue;
     const size_t smem = kFrameSmemBytes;
     switch (BB) {
-        case 4: frame_phase_kernel<4><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
-        case 8: frame_phase_kernel<8><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
-        case 10: frame_phase_kernel<10><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
-        case 16: frame_phase_kernel<16><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
-        default: frame_phase_kernel<32><<<items, kFrameThreads, smem, st>>>(s, d, v_tap0, normalize, FC); break;
+        case 4: frame_launch<4>(s, d, v_tap0, normalize, FC, items, smem, st); break;
+        case 8: frame_launch<8>(s, d, v_tap0, normalize, FC, items, smem, st); break;
+        case 10: frame_launch<10>(s, d, v_tap0, normalize, FC, items, smem, st); break;
+        case 16: frame_launch<16>(s, d, v_tap0, normalize, FC, items, smem, st); break;
+        default: frame_launch<32>(s, d, v_tap0, normalize, FC, items, smem, st); break;
     }
     return cudaGetLastError();
 }

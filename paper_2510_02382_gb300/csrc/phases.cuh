@@ -633,12 +633,13 @@ struct ScaleJob {
 //   1/lambda for the next iteration with T'' = T' scale_{(n,0)}^2.
 // Threads: tx = tid & 7 frame of the tile, ty = tid >> 3 bin slice (one frame per thread:
 // the variant for many bases, BB = 32).
-template <int BB>
+template <int BB, bool EXACT = false>
 __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, const int item, const Grp& g,
                                            float* gsm, const int FC, const float* scale, const int v_tap0,
                                            const ScaleJob* job = nullptr)
 {
-    const int M = s.M, N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
+    const int M = s.M, N = s.N, F = s.F, J = s.J, Jp = s.Jp;
+    const int B = EXACT ? BB : s.B;     // EXACT: the bases count is the class width
     (void)M;
     const int ntiles = Jp / kFrameTile;
     const int n = item / ntiles, tile = item - n * ntiles;
@@ -762,13 +763,14 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
 // memory feeds the two frames' PSD and both sums, and the reduction over the 8 bin slices
 // of a warp is a three-level reduce-scatter. Threads: tx = tid & 3 owns frames j0 + 2tx
 // and j0 + 2tx + 1, ty = tid >> 2 is the bin slice.
-template <int BB>
+template <int BB, bool EXACT = false>
 __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
                                            float* gsm, const int FC, const float* scale, const int v_tap0,
                                            const ScaleJob* job = nullptr)
 {
     static_assert(BB % 2 == 0 && BB <= 16, "two-frame item needs an even BB <= 16");
-    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp;
+    const int N = s.N, F = s.F, J = s.J, Jp = s.Jp;
+    const int B = EXACT ? BB : s.B;     // EXACT: the bases count is the class width (no per-k tests)
     const int ntiles = Jp / kFrameTile;
     const int n = item / ntiles, tile = item - n * ntiles;
     const int j0 = tile * kFrameTile;
