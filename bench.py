@@ -86,7 +86,7 @@ def workload_config(spec, l2_note):
 
 KERNEL_SOURCES = {   # the CUDA sources each profiled kernel is compiled from (besides the common headers)
     "persistent_kernel": lambda f: f == "persistent_kernel.cuh" or f.startswith("persistent"),
-    "bin_phase_kernel": lambda f: f == "bin_phase.cu",
+    "bin_phase_kernel": lambda f: f.startswith("bin_phase"),   # bin_phase.cu, bin_phase_kernels.cuh, bin_phase_m*.cu
     "frame_phase_kernel": lambda f: f == "kernels.cu",
 }
 
