@@ -58,3 +58,30 @@ def test_long_j_workload_one_iteration():
     ref = run_oracle(mix, 1)
     assert rel_fro(got["y"], ref["y"]) < 1e-4
     assert rel_fro(got["T"], ref["b"]) < 1e-4 and rel_fro(got["V"], ref["v"]) < 1e-4
+
+
+# the size limits of the two bin-phase forms: the largest bin one block holds (8 frames x
+# 512 threads for M <= 4, 4 x 256 for M = 5..8), the first frame past it (a cluster of two
+# blocks with a ragged second chunk), and the largest bin a cluster of 8 blocks holds
+LIMIT_SHAPES = [
+    # (M, N, Ln, F, J, B)
+    (4, 2, (2, 2), 2, 4096, 4),        # one block, every thread full
+    (6, 2, (3, 3), 2, 1024, 3),        # one block, M = 5..8
+    (3, 2, (2, 1), 2, 4097, 3),        # cluster of 2, one frame in the last chunk row
+    (7, 3, (3, 2, 2), 1, 1025, 3),     # cluster of 2, M = 5..8
+    (3, 2, (2, 1), 1, 16384, 3),       # cluster of 8, M = 3..8 limit
+    (2, 2, (1, 1), 1, 32768, 2),       # cluster of 8, M = 2 limit
+]
+
+
+@pytest.mark.parametrize("shape", LIMIT_SHAPES, ids=lambda s: f"M{s[0]}J{s[4]}")
+def test_size_limits_one_iteration(shape):
+    M, N, Ln, F, J, B = shape
+    mix = synth.random_case(4000 + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+    got = run_gpu(mix, 1, path="two_kernel")
+    ref = run_oracle(mix, 1)
+    assert rel_fro(got["y"], ref["y"]) < 1e-4
+    assert rel_fro(got["W"], ref["W"]) < 1e-4
+    assert rel_fro(got["T"], ref["b"]) < 1e-4 and rel_fro(got["V"], ref["v"]) < 1e-4
+    assert abs(got["logdet"] - ref["logdet"]).max() < 1e-4
+    assert rel_fro(got["images"], ref["images"]) < 1e-4
