@@ -33,8 +33,13 @@ __host__ __device__ inline ClusterSmem cluster_smem_layout(int M, int N, int B, 
     return L;
 }
 
+// Blocks per SM the register budget is sized for: two when a thread's rows are fewer than 16
+// complex values (64 registers), so that one cluster's barrier waits overlap another's work.
 template <int M, int FPT>
-__global__ void __launch_bounds__(kClusterThreads, 1)
+constexpr int cluster_min_blocks() { return M * FPT < 16 ? 2 : 1; }
+
+template <int M, int FPT>
+__global__ void __launch_bounds__(kClusterThreads, cluster_min_blocks<M, FPT>())
 cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
 {
     constexpr int NV = 3 * M - 2;                   // d_p (M real), n_p for p != r (M-1 complex)
