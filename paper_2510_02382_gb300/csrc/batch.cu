@@ -30,7 +30,7 @@ constexpr int kBatchFrameSmemBytes = 48 * 1024;
 
 // EXACT: every mixture of the launch has B equal to the class width BB.
 template <int BB, bool EXACT>
-__global__ void __launch_bounds__(kBatchFrameThreads)
+__global__ void __launch_bounds__(kBatchFrameThreads, frame_min_blocks<BB>())
 batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ work, const int v_tap0,
                    const int normalize)
 {

@@ -567,6 +567,14 @@ __device__ __forceinline__ void load_bin(const int Jp, const float2* Ysrc, const
 template <int BB>
 __host__ __device__ inline int frame_smem_fixed(int nt) { return (nt / 32) * 2 * BB * kFrameTile + BB * kFrameTile; }
 
+// Blocks per SM the batched frame kernel's register budget is sized for (256 threads):
+// three up to 10 bases (80 registers, a few spilled; the 48 KB staging area also allows
+// three), else the compiler's choice (the 16- and 32-wide accumulators would spill under a
+// cap). The single-mixture frame kernel keeps the compiler's choice: its (tile, source)
+// items rarely fill two blocks per SM, so the spills would cost without a gain.
+template <int BB>
+constexpr int frame_min_blocks() { return BB <= 10 ? 3 : 1; }
+
 __host__ __device__ inline int frame_chunk(int avail_floats, int B, int fixed)
 {
     return ((avail_floats - fixed) / (B + kFrameTile)) & ~3;   // multiple of 4: Ps stays 16-byte aligned
