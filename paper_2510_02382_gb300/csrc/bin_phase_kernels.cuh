@@ -120,10 +120,10 @@ template <int M, int FPT>
 inline cudaError_t launch_ip_mf(const Shape& s, const State& d, int v_tap0, int nt, cudaStream_t st, bool cfg)
 {
     // the covariance sums hold M (M + 1) / 2 complex partials per frame and the FP64 solve
-    // runs on warp 0 with a few doubles per lane: 80 registers (three 256-thread blocks per
-    // SM) below 8 frames per thread
+    // runs on warp 0 with a few doubles per lane: 64 registers (four 256-thread blocks per
+    // SM, so that 4 x 152 blocks cover 513 bins in one wave) below 8 frames per thread
     constexpr int kMaxT = FPT == 8 ? 512 : 256;
-    constexpr int kMinB = FPT == 8 ? 1 : 3;
+    constexpr int kMinB = FPT == 8 ? 1 : 4;
     if (cfg) {
         int dev = 0, optin = 0;
         cudaError_t e = cudaGetDevice(&dev);
