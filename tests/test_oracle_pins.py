@@ -211,6 +211,34 @@ def test_mu_sums_are_the_gradient_split():
         assert abs(g - (den_v[idx] - num_v[idx])) < 1e-5 * max(1.0, abs(g))
 
 
+def test_mu_single_basis_is_the_geometric_mean_step():
+    """With one basis (K = 1) the NLL of Eq. 5 in b_{n,i} (or in v_{n,j}) has the closed-form
+    minimiser b* = mean over the unmasked (j, l) terms of |y_{(n,l),i,j}|^2 / v_{n,j-l}
+    (v* = mean over (i, l) of |y_{(n,l),i,j+l}|^2 / b_{n,i}); the majorise-minimise steps of
+    Eqs. 17-18 move halfway there in log scale: b_new = sqrt(b b*), v_new = sqrt(v v*)."""
+    Ln = (2, 1)
+    rng = np.random.default_rng(17)
+    I, J = 3, 15
+    b = rng.uniform(0.3, 2.0, (2, I, 1))
+    v = rng.uniform(0.3, 2.0, (2, 1, J))
+    y = rng.standard_normal((3, I, J)) + 1j * rng.standard_normal((3, I, J))
+    rows = [(0, 0), (0, 1), (1, 0)]
+    for n in range(2):
+        taps = [(r, l) for r, (nn, l) in enumerate(rows) if nn == n]
+        bstar = np.zeros(I)
+        for i in range(I):
+            terms = [abs(y[r, i, j]) ** 2 / v[n, 0, j - l] for r, l in taps for j in range(l, J)]
+            bstar[i] = np.mean(terms)
+        vstar = np.zeros(J)
+        for j in range(J):
+            terms = [abs(y[r, i, j + l]) ** 2 / b[n, i, 0] for r, l in taps for i in range(I) if j + l < J]
+            vstar[j] = np.mean(terms)
+        b_new, _, _ = O.update_basis(b, v, y, Ln)
+        v_new, _, _ = O.update_activation(b, v, y, Ln, "all_taps")
+        assert np.max(np.abs(b_new[n, :, 0] / np.sqrt(b[n, :, 0] * bstar) - 1)) < 1e-12
+        assert np.max(np.abs(v_new[n, 0] / np.sqrt(v[n, 0] * vstar) - 1)) < 1e-12
+
+
 def test_tap0_mode_equals_all_taps_when_one_tap():
     Ln = (1, 1)
     mix, x, W, b, v = _small(seed=8, M=2, N=2, Ln=Ln, F=3, J=12)
