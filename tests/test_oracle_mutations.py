@@ -1,11 +1,11 @@
 """The oracle's pins catch plausible mistakes (CPU only).
 
 Each case below plants one mistake in a copy of one oracle function (a dropped term, a
-conjugate, a wrong delay index, a transposed operand, a missing factor), installs it in
-place of the original for the duration of the test, and runs every pin of
-test_oracle_pins.py against the mutated oracle. At least one pin must fail; otherwise the
-pins would not tell that oracle apart from the correct one, and the GPU parity that rests
-on the oracle would prove nothing about that part of the method.
+conjugate, a wrong delay index, a transposed operand, a missing factor, a step taken on
+stale values), installs it in place of the original for the duration of the test, and runs
+every pin of test_oracle_pins.py against the mutated oracle. At least one pin must fail;
+otherwise the pins would not tell that oracle apart from the correct one, and the GPU
+parity that rests on the oracle would prove nothing about that part of the method.
 """
 import itertools
 
@@ -149,7 +149,80 @@ def _source_images_transposed_H(W, y, Ln):
     return out
 
 
+def _iterate(stale_bases=False, stale_rows=False):
+    """One iteration with an ordering mistake: the activation update with the bases from
+    before the basis update, or both NMF updates on the rows from before the demixing update."""
+    def iterate(x, W, b, v, Ln, update="iss", v_mode="all_taps", normalize=True):
+        lam = O.psd(b, v)
+        y_old = O.demix(W, x)
+        Q = O.weighted_covariances(x, O.delayed_weights(lam, Ln))
+        W, _ = O.iss_sweep(W, Q) if update == "iss" else (O.ip_sweep(W, Q), None)
+        y = O.demix(W, x)
+        yn = y_old if stale_rows else y
+        b_new, _, _ = O.update_basis(b, v, yn, Ln)
+        v, _, _ = O.update_activation(b if stale_bases else b_new, v, yn, Ln, v_mode)
+        b = b_new
+        if normalize:
+            y, W, b, _ = O.normalise(y, W, b, Ln)
+        return W, b, v, y
+    return iterate
+
+
+def _iss_sweep_gauss_seidel(W, Q):
+    """ISS with the rows updated one p at a time inside a step, so that later z_p of the same
+    step see the already-updated rows (the step's z must all come from the same W)."""
+    W = W.copy()
+    I, M, _ = W.shape
+    zs = []
+    for r in range(M):
+        z = np.zeros((I, M), dtype=complex)
+        for p in range(M):
+            wr_h = W[:, r, :].copy()
+            den = np.einsum("im,imk,ik->i", wr_h, Q[p], wr_h.conj()).real
+            ok = den > 0
+            if p != r:
+                num = np.einsum("im,imk,ik->i", W[:, p, :], Q[p], wr_h.conj())
+                z[ok, p] = num[ok] / den[ok]
+            else:
+                z[ok, p] = 1.0 - 1.0 / np.sqrt(den[ok])
+            W[:, p, :] = W[:, p, :] - z[:, p, None] * wr_h
+        zs.append(z)
+    return W, zs
+
+
+def _ip_sweep_reversed_product(W, Q):
+    """IP of Eqs. 9-10 solving (Q_r W) w = e_r instead of (W Q_r) w = e_r."""
+    W = W.copy()
+    I, M, _ = W.shape
+    for r in range(M):
+        e = np.eye(M, dtype=complex)[r]
+        for i in range(I):
+            w = np.linalg.solve(Q[r, i] @ W[i], e)
+            W[i, r, :] = (w / np.sqrt((w.conj() @ Q[r, i] @ w).real)).conj()
+    return W
+
+
+def _weighted_covariances_without_1_over_J(x, phi):
+    """Q_r of Eq. 8 without its 1/J."""
+    return np.einsum("rij,imj,ikj->rimk", phi, x, x.conj())
+
+
+_NORMALISE = O.normalise      # the unmutated function, captured before any test patches it
+
+
+def _normalise_columns(y, W, b, Ln):
+    """Eqs. 19-21 with the columns of W divided by mu instead of its rows."""
+    y2, _, b2, mu = _NORMALISE(y, W, b, Ln)
+    return y2, W / mu[None, None, :], b2, mu
+
+
 MUTANTS = {
+    "iterate_activation_with_stale_bases": {"iterate": _iterate(stale_bases=True)},
+    "iterate_nmf_on_rows_before_the_sweep": {"iterate": _iterate(stale_rows=True)},
+    "iss_rows_updated_within_a_step": {"iss_sweep": _iss_sweep_gauss_seidel},
+    "ip_reversed_product": {"ip_sweep": _ip_sweep_reversed_product},
+    "covariance_without_1_over_J": {"weighted_covariances": _weighted_covariances_without_1_over_J},
+    "normalise_columns_of_W": {"normalise": _normalise_columns},
     "iss_conjugate_numerator": {"iss_sweep": _iss_sweep(conj_num=True)},
     "iss_conjugated_row_update": {"iss_sweep": _iss_sweep(conj_update=True)},
     "ip_without_scaling": {"ip_sweep": _ip_sweep_unscaled},

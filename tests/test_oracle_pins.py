@@ -239,6 +239,41 @@ def test_mu_single_basis_is_the_geometric_mean_step():
         assert np.max(np.abs(v_new[n, 0] / np.sqrt(v[n, 0] * vstar) - 1)) < 1e-12
 
 
+def test_iteration_order_single_basis():
+    """One whole iteration without normalisation, one basis (Sec. III order: demixing
+    update, then the basis update on the new rows, then the activation update with the new
+    bases): with y = W x from the returned W, the returned b is sqrt(b0 b*) with b* the
+    closed-form minimiser for y and v0, and the returned v is sqrt(v0 v*) with v* the one
+    for y and the returned b."""
+    Ln = (2, 1)
+    mix = synth.random_case(19, M=3, N=2, F=4, J=18, B=1, Ln=Ln)
+    x, W0, b0, v0 = O.init_state(mix.X, mix.T0, mix.V0)
+    W, b, v, y = O.iterate(x, W0, b0, v0, Ln, normalize=False)
+    y = O.demix(W, x)
+    rows = O.row_map(Ln)
+    I, J = x.shape[0], x.shape[2]
+    for n in range(2):
+        taps = [(r, l) for r, (nn, l) in enumerate(rows) if nn == n]
+        bstar = np.array([np.mean([abs(y[r, i, j]) ** 2 / v0[n, 0, j - l] for r, l in taps for j in range(l, J)])
+                          for i in range(I)])
+        vstar = np.array([np.mean([abs(y[r, i, j + l]) ** 2 / b[n, i, 0] for r, l in taps for i in range(I)
+                                   if j + l < J]) for j in range(J)])
+        assert np.max(np.abs(b[n, :, 0] / np.sqrt(b0[n, :, 0] * bstar) - 1)) < 1e-12
+        assert np.max(np.abs(v[n, 0] / np.sqrt(v0[n, 0] * vstar) - 1)) < 1e-12
+
+
+@pytest.mark.parametrize("Ln,M,N", [((2, 1), 3, 2), ((2, 1, 1), 4, 3), ((2, 2), 4, 2)])
+def test_nll_nonincreasing_over_whole_iterations(Ln, M, N):
+    """Without the normalisation every iteration is a chain of majorise-minimise steps of
+    Eq. 5 (demixing update, basis MU, activation MU), so the NLL never rises."""
+    mix = synth.random_case(30 + M + N, M=M, N=N, F=4, J=24, B=3, Ln=Ln)
+    x, W, b, v = O.init_state(mix.X, mix.T0, mix.V0)
+    out = O.run(mix.X, Ln, mix.T0, mix.V0, 12, normalize=False, trace=True)
+    c = [O.nll(O.demix(W, x), O.psd(b, v), W, Ln)] + list(out["trace"])
+    for a, bb in zip(c[:-1], c[1:]):
+        assert bb <= a + 1e-9 * abs(a), (a, bb)
+
+
 def test_tap0_mode_equals_all_taps_when_one_tap():
     Ln = (1, 1)
     mix, x, W, b, v = _small(seed=8, M=2, N=2, Ln=Ln, F=3, J=12)
