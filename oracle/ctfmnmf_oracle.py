@@ -56,7 +56,8 @@ def demix(W, x):
 
 
 def delayed_weights(lam, Ln):
-    """phi[r,i,j] = 1 / lambda_{n,i,j-l} for j >= l, 0 for the masked j < l."""
+    """phi[r,i,j] = 1 / lambda_{n,i,j-l} for j >= l, 0 for the masked j < l: the weight of
+    extended row r = (n, l) in Eq. 8 (the delayed PSD of the extended model, Sec. II)."""
     N, I, J = lam.shape
     rows = row_map(Ln)
     phi = np.zeros((len(rows), I, J))
@@ -124,7 +125,8 @@ def ip_sweep(W, Q):
 
 
 def _delayed_power(y, Ln, n, J):
-    """P[i,j'] = sum_{l < L_n, j'+l < J} |y_{(n,l),i,j'+l}|^2 and the count of valid l."""
+    """P[i,j'] = sum_{l < L_n, j'+l < J} |y_{(n,l),i,j'+l}|^2 and the count of valid l: the
+    delayed power of source n that the all-taps reading of Eq. 18 uses."""
     rows = row_map(Ln)
     I = y.shape[1]
     P = np.zeros((I, J))
@@ -198,6 +200,7 @@ def normalise(y, W, b, Ln):
 
 
 def logabsdet(W):
+    """log|det W_i| per bin (the log-determinant term of Eq. 5), by LU."""
     return np.linalg.slogdet(W)[1]
 
 
@@ -257,7 +260,9 @@ def init_state(x_mfj, b0, v0):
 
 
 def iterate(x, W, b, v, Ln, update="iss", v_mode="all_taps", normalize=True):
-    """One iteration: W update (ISS or IP) -> basis MU -> activation MU -> normalisation."""
+    """One iteration in the order of Sec. III: W update (ISS, Eqs. 11-16, or IP, Eqs. 9-10)
+    -> basis MU (Eq. 17) on the new rows -> activation MU (Eq. 18) with the new bases ->
+    normalisation (Eqs. 19-21)."""
     lam = psd(b, v)
     Q = weighted_covariances(x, delayed_weights(lam, Ln))
     if update == "iss":
@@ -275,7 +280,7 @@ def iterate(x, W, b, v, Ln, update="iss", v_mode="all_taps", normalize=True):
 
 
 def run(x_mfj, Ln, b0, v0, n_iter, update="iss", v_mode="all_taps", normalize=True, trace=False):
-    """Run n_iter iterations from W = I. x_mfj is [M][I][J] (per-microphone STFTs).
+    """Run n_iter iterations from W = I (Sec. IV-A). x_mfj is [M][I][J] (per-microphone STFTs).
 
     Returns a dict with W [I][M][M], y [M][I][J], b, v, cost, logdet [I] and,
     when trace is set, the cost after every iteration.
