@@ -26,13 +26,14 @@ batch_bin_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ wor
     const State& d = md.d;
     const int i = w.y;
     const Grp g{(int)threadIdx.x, (int)blockDim.x, 0};
-    if (threadIdx.x < CTFMNMF_MAX_M) s_scale[threadIdx.x] = (int)threadIdx.x < M ? d.scale[threadIdx.x] : 1.f;
-    __syncthreads();
     float2 y[M][FPT];
     float2 wcol[M];
     float2* Yb = d.Y + (size_t)i * M * s.Jp;
     float2* Wb = d.W + (size_t)i * M * M;
-    load_bin<M, FPT, true>(s.Jp, Yb, Wb, g, s_scale, y, wcol);
+    load_bin_unscaled<M, FPT>(s.Jp, Yb, Wb, g, y, wcol);     // in flight while the scale arrives
+    if (threadIdx.x < CTFMNMF_MAX_M) s_scale[threadIdx.x] = (int)threadIdx.x < M ? d.scale[threadIdx.x] : 1.f;
+    __syncthreads();
+    apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
     const float detf = bin_body<M, FPT, true, KB>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
     if (g.tid == 0) {
         double f = (double)detf;

@@ -204,7 +204,8 @@ __device__ __forceinline__ void ip_solve_warp(const float* Qs, float2* W, float*
 // IP = true replaces the ISS sweep by the IP update of Eqs. 9-10 (M <= 4): the weighted
 // covariances Q_r (Eq. 8) of the kept observation d.X, the sequential solves (ip_solve_warp),
 // then y = W x; the return value is then |det W_new| / |det W_old|.
-template <int M, int FPT, bool GLOBAL, int KB = 16, bool IP = false>
+// VPRE = true loads the first V column of the basis update ahead of the barrier before it.
+template <int M, int FPT, bool GLOBAL, int KB = 16, bool IP = false, bool VPRE = false>
 __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const int i, const Grp& g,
                                           float* gsm, float2 (&y)[M][FPT], float2 (&wcol)[M],
                                           float2* Ydst, float2* Wdst, const float* scale, const int v_tap0)
@@ -233,11 +234,12 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         const float4* src = reinterpret_cast<const float4*>(d.invlam + (size_t)i * N * Jp);
         float4* dst = reinterpret_cast<float4*>(ils);
         const int LR4 = LR >> 2, J4 = Jp >> 2, P4 = kLPad >> 2;
-        for (int e = g.tid; e < N * LR4; e += g.nt) {
-            const int n = e / LR4, o = e - n * LR4;
-            if (o < P4) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            else cp_async16(dst + e, src + (size_t)n * J4 + o - P4);
-        }
+        for (int n = 0; n < N; ++n)
+            for (int o = g.tid; o < LR4; o += g.nt) {
+                const int e = n * LR4 + o;
+                if (o < P4) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                else cp_async16(dst + e, src + (size_t)n * J4 + o - P4);
+            }
         cp_async_wait();
     }
     grp_sync(g);
@@ -434,6 +436,18 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
             else Wdst[p * M + g.tid] = wcol[p];
         }
     }
+    // VPRE: the first column of the first basis-update pass (source 0, bases 0 .. KB-1) into
+    // registers now, so that its load overlaps the delayed-power step instead of following
+    // the barrier after it (for 8 frames per thread: the rows' registers are free here)
+    constexpr bool kVpre = VPRE && FPT == 8 && KB <= 10;
+    const int J4 = Jp >> 2;
+    float4 vpre[kVpre ? KB : 1];
+    if constexpr (kVpre) {
+        const float4* V0 = reinterpret_cast<const float4*>(d.V);
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+            vpre[k] = (g.tid < J4 && k < B) ? V0[(size_t)k * J4 + g.tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     grp_sync(g);
 
     // ---- delayed power and the basis-update weights at this thread's frames; the
@@ -469,7 +483,6 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
     //      columns (float4 loads of V through the L1, which the groups of a CTA share; the
     //      grid barrier's acquire orders them after the previous frame phase), then a
     //      reduce-scatter per 16 bases
-    const int J4 = Jp >> 2;
     for (int n = 0; n < N; ++n) {
         const float4* A4 = reinterpret_cast<const float4*>(ils + n * LR + kLPad);
         const float4* C4 = reinterpret_cast<const float4*>(Cw + n * Jp);
@@ -478,7 +491,24 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
 #pragma unroll
             for (int k = 0; k < 32; ++k) a[k] = 0.f;
             const float4* Vn = reinterpret_cast<const float4*>(d.V + ((size_t)n * B + kb) * Jp);
-            for (int q = g.tid; q < J4; q += g.nt) {
+            int q = g.tid;
+            if constexpr (kVpre) {
+                if (n == 0 && kb == 0) {          // this thread's first column: the prefetched V
+                    if (q < J4) {
+                        const float4 A = A4[q], C = C4[q];
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) {
+                            if (k < B) {
+                                const float4 v = vpre[k];
+                                a[k] = fmaf(v.x, A.x, fmaf(v.y, A.y, fmaf(v.z, A.z, fmaf(v.w, A.w, a[k]))));
+                                a[16 + k] = fmaf(v.x, C.x, fmaf(v.y, C.y, fmaf(v.z, C.z, fmaf(v.w, C.w, a[16 + k]))));
+                            }
+                        }
+                    }
+                    q += g.nt;
+                }
+            }
+            for (; q < J4; q += g.nt) {
                 const float4 A = A4[q], C = C4[q];
 #pragma unroll
                 for (int k = 0; k < KB; ++k) {
@@ -558,6 +588,42 @@ __device__ __forceinline__ void load_bin(const int Jp, const float2* Ysrc, const
             const float2 w = GLOBAL ? __ldcg(Wsrc + p * M + g.tid) : Wsrc[p * M + g.tid];
             wcol[p] = make_float2(w.x * scale[p], w.y * scale[p]);
         }
+    }
+}
+
+// load_bin in two halves, so that the row loads need not wait for the pending scale: the
+// unscaled rows (frames g.tid + f*g.nt; zero past Jp) and column g.tid < M of W_i from
+// HBM/L2 first, then, once the scale is in shared memory, the multiplication.
+template <int M, int FPT>
+__device__ __forceinline__ void load_bin_unscaled(const int Jp, const float2* Ysrc, const float2* Wsrc, const Grp& g,
+                                                  float2 (&y)[M][FPT], float2 (&wcol)[M])
+{
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int j = g.tid + f * g.nt;
+            y[r][f] = j < Jp ? __ldcg(Ysrc + (size_t)r * Jp + j) : make_float2(0.f, 0.f);
+        }
+    if (g.tid < M) {
+#pragma unroll
+        for (int p = 0; p < M; ++p) wcol[p] = __ldcg(Wsrc + p * M + g.tid);
+    }
+}
+
+template <int M, int FPT>
+__device__ __forceinline__ void apply_bin_scale(const Grp& g, const float* scale, float2 (&y)[M][FPT],
+                                                float2 (&wcol)[M])
+{
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        const float sc = scale[r];
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) y[r][f] = make_float2(y[r][f].x * sc, y[r][f].y * sc);
+    }
+    if (g.tid < M) {
+#pragma unroll
+        for (int p = 0; p < M; ++p) wcol[p] = make_float2(wcol[p].x * scale[p], wcol[p].y * scale[p]);
     }
 }
 
