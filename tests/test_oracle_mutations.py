@@ -103,6 +103,30 @@ def _update_activation_no_count(b, v, y, Ln, mode="all_taps"):
     return np.maximum(v * np.sqrt(num / den), O.FLOOR_NMF), num, den
 
 
+_UPDATE_ACTIVATION = O.update_activation   # the unmutated function
+
+
+def _update_activation_tap0(wrong_row=False, all_tap_count=False):
+    """Eq. 18 as printed (tap 0) with a planted mistake: the last tap's row of the source in
+    place of its tap-0 row, or the all-taps count of valid taps kept in the denominator."""
+    def update(b, v, y, Ln, mode="all_taps"):
+        if mode != "tap0":
+            return _UPDATE_ACTIVATION(b, v, y, Ln, mode)
+        lam = O.psd(b, v)
+        N, K, J = v.shape
+        rows = O.row_map(Ln)
+        num = np.zeros_like(v)
+        den = np.zeros_like(v)
+        for n in range(N):
+            r = rows.index((n, Ln[n] - 1 if wrong_row else 0))
+            P = np.abs(y[r]) ** 2
+            cnt = O._delayed_power(y, Ln, n, J)[1] if all_tap_count else np.ones(J)
+            num[n] = np.einsum("ik,ij->kj", b[n], P / lam[n] ** 2)
+            den[n] = np.einsum("ik,ij->kj", b[n], cnt[None, :] / lam[n])
+        return np.maximum(v * np.sqrt(num / den), O.FLOOR_NMF), num, den
+    return update
+
+
 def _delayed_power_backwards(y, Ln, n, J):
     """Delayed power with the delay applied in the wrong direction: |y_{(n,l),j-l}|^2 at j."""
     I = y.shape[1]
@@ -231,6 +255,8 @@ MUTANTS = {
     "basis_mu_lambda_inverse_for_inverse_square": {"update_basis": _update_basis(power=1)},
     "basis_mu_without_sqrt": {"update_basis": _update_basis(root=False)},
     "activation_mu_without_tap_count": {"update_activation": _update_activation_no_count},
+    "activation_tap0_wrong_tap_row": {"update_activation": _update_activation_tap0(wrong_row=True)},
+    "activation_tap0_all_taps_count": {"update_activation": _update_activation_tap0(all_tap_count=True)},
     "delayed_power_backwards": {"_delayed_power": _delayed_power_backwards},
     "normalise_b_by_mu": {"normalise": _normalise_b_by_mu},
     "cost_without_J": {"nll": _nll_without_J},

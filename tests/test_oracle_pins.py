@@ -283,6 +283,26 @@ def test_tap0_mode_equals_all_taps_when_one_tap():
     assert np.max(np.abs(v1 - v2)) < 1e-14
 
 
+def test_tap0_single_basis_is_the_geometric_mean_step():
+    """Eq. 18 as printed (tap 0 only), one basis (K = 1), sources with more than one tap:
+    with lambda = b v the update reads v_new = v sqrt(sum_i |y_{(n,0),i,j}|^2 / (b_{n,i} v^2)
+    / sum_i 1/v), i.e. the geometric mean of v and the minimiser v* = mean over bins i of
+    |y_{(n,0),i,j}|^2 / b_{n,i} of the tap-0 terms of Eq. 5. Only row (n, 0) enters and the
+    denominator counts one term per bin, whatever L_n is."""
+    Ln = (3, 2)
+    rows = O.row_map(Ln)
+    rng = np.random.default_rng(23)
+    I, J = 4, 11
+    b = rng.uniform(0.3, 2.0, (2, I, 1))
+    v = rng.uniform(0.3, 2.0, (2, 1, J))
+    y = rng.standard_normal((5, I, J)) + 1j * rng.standard_normal((5, I, J))
+    v_new, _, _ = O.update_activation(b, v, y, Ln, "tap0")
+    for n in range(2):
+        r0 = rows.index((n, 0))
+        vstar = np.array([np.mean([abs(y[r0, i, j]) ** 2 / b[n, i, 0] for i in range(I)]) for j in range(J)])
+        assert np.max(np.abs(v_new[n, 0] / np.sqrt(v[n, 0] * vstar) - 1)) < 1e-12
+
+
 def test_nmf_factors_stay_positive():
     Ln = (2, 1)
     mix = synth.random_case(12, M=3, N=2, F=6, J=30, B=3, Ln=Ln)
@@ -433,7 +453,7 @@ def test_single_tap_case_matches_data_domain_iss():
     assert np.max(np.abs(O.demix(W2, x) - y)) < 1e-10 * np.max(np.abs(y))
 
 
-# --- Table I (Sec. IV-A): taps per source for 4/6/8 microphones and 2 sources
+# --- Table I (Sec. V-A): taps per source for 4/6/8 microphones and 2 sources
 
 def test_default_taps_reproduce_table1():
     rows = np.loadtxt(os.path.join(HERE, "golden", "table1_taps.txt"), dtype=int)
