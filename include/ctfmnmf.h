@@ -9,7 +9,7 @@
  *   - NMF source model lambda_{n,i,j} = sum_k T[n,i,k] V[n,k,j]                    (Sec. II)
  *   - negative log-likelihood                                                     (Eq. 5)
  *   - ISS rank-1 updates W_i <- W_i - z_r w_r^H with the closed form of Eq. 16    (Sec. III-A)
- *   - multiplicative updates of T (Eq. 17) and V (Eq. 18), scale normalisation    (Sec. III-B)
+ *   - multiplicative updates of T (Eq. 17) and V (Eq. 18), scale normalisation    (Sec. III-A)
  *   - source images by the multichannel Wiener filter                            (Eqs. 23-24)
  *
  * Conventions for every entry point:
@@ -148,7 +148,7 @@ int ctfmnmf_get_taps(ctfmnmf_t h, int* Ln);
 /*
  * Load the observed STFT X (device pointer, complex64 [M][F][J], read only during the
  * call's stream work) and reset the demixing state: W_i = I, y = x, log|det W_i| = 0
- * (initialisation of Sec. IV-A). T and V are not changed: they keep the default init of
+ * (initialisation of Sec. V-A). T and V are not changed: they keep the default init of
  * ctfmnmf_create, the values of ctfmnmf_set_init or the result of earlier iterations.
  * Synchronises the stream to check X:
  * ENONFINITE if X holds NaN or Inf (the state is then unusable until a good load).

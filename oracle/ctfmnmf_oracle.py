@@ -250,7 +250,7 @@ def mwf_images(W, lam, x, Ln):
 
 
 def init_state(x_mfj, b0, v0):
-    """Initial state: W_i = I (Sec. IV-A), y = x, and the given NMF factors."""
+    """Initial state: W_i = I (Sec. V-A), y = x, and the given NMF factors."""
     x = np.transpose(np.asarray(x_mfj, dtype=complex), (1, 0, 2))    # [I][M][J]
     I, M, J = x.shape
     W = np.tile(np.eye(M, dtype=complex), (I, 1, 1))
@@ -280,7 +280,7 @@ def iterate(x, W, b, v, Ln, update="iss", v_mode="all_taps", normalize=True):
 
 
 def run(x_mfj, Ln, b0, v0, n_iter, update="iss", v_mode="all_taps", normalize=True, trace=False):
-    """Run n_iter iterations from W = I (Sec. IV-A). x_mfj is [M][I][J] (per-microphone STFTs).
+    """Run n_iter iterations from W = I (Sec. V-A). x_mfj is [M][I][J] (per-microphone STFTs).
 
     Returns a dict with W [I][M][M], y [M][I][J], b, v, cost, logdet [I] and,
     when trace is set, the cost after every iteration.

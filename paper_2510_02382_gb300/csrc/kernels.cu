@@ -7,7 +7,7 @@
 
 namespace ctf {
 
-// ------------------------------------------------------------------ load (Sec. IV-A init)
+// ------------------------------------------------------------------ load (Sec. V-A init)
 // Y[i][m][j] = X[m][i][j] (W_i = I so y = x), zero padding frames; W = I, log|det| = 0,
 // pending scale 1. flag[0] is set if X holds a non-finite value.
 __global__ void load_kernel(const Shape s, const State d, const float2* __restrict__ X)
