@@ -336,12 +336,12 @@ int ctfmnmf_grad_launch_count(ctfmnmf_grad_t g, long long* count);
 int ctfmnmf_grad_destroy(ctfmnmf_grad_t g);
 
 /*
- * ctfmnmf_cost_noalloc -- the negative log-likelihood of Eq. 5 (as ctfmnmf_cost) from
- * caller-held buffers, without allocating any device memory. The paper has no counterpart:
- * this entry point exists for callers that cannot call cudaMalloc where they need the
- * cost, e.g. code that runs while a CUDA graph is being captured on its stream, code inside
- * an allocator or memory-pool callback, or an application whose device memory is owned by
- * another framework.
+ * ctfmnmf_cost_noalloc -- the same negative log-likelihood as ctfmnmf_cost, computed from
+ * caller-held buffers without allocating any device memory. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc where they need the cost,
+ * e.g. a real-time audio thread (an allocation may synchronise the device and has no
+ * latency bound), code inside an allocator or memory-pool callback (it would re-enter the
+ * allocator), or an application whose device memory is owned by another framework.
  *   Y [M][F][J] complex64, T [N][F][B] and V [N][B][J] float32, logdet [F] float64: device
  *   pointers in the layouts of ctfmnmf_get_demixed / _get_nmf / _get_logdet (read only);
  *   Ln[N]: host array of taps (sum M); out: device pointer to one double (written);
@@ -350,8 +350,10 @@ int ctfmnmf_grad_destroy(ctfmnmf_grad_t g);
  * Scratch: the per-bin partial sums live in a 128 KiB static device array that every GPU
  * loading the library holds until exit. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture. All calls share the array: calls whose kernels overlap on the GPU
- * (different streams or threads without ordering) race and give wrong results.
+ * stream capture. A device reset gives the device a new context, and the next call looks
+ * the address up again. All calls share the array, and each call overwrites the slots it
+ * uses: calls whose kernels overlap on the GPU (different streams or threads without
+ * ordering) race and give wrong results.
  * Errors: EINVAL (dimensions, taps, null pointers, F too large), ECUDA (launch failed).
  */
 int ctfmnmf_cost_noalloc(int M, int N, const int* Ln, int B, int F, int J, const void* Y,

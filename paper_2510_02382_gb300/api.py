@@ -255,9 +255,23 @@ def cost_noalloc(Y, T, V, logdet, Ln, out, stream=None):
     the device), without any device allocation by the library. Y [M][F][J] complex64,
     T [N][F][B], V [N][B][J] float32, logdet [F] float64."""
     import torch
+    # the C side trusts every size it is given: check them all here, before any launch
+    if Y.dim() != 3 or T.dim() != 3:
+        raise ValueError("Y must be [M][F][J] and T [N][F][B]")
     M, F, J = Y.shape
     N, _, B = T.shape
+    if len(Ln) != N:
+        raise ValueError(f"Ln has {len(Ln)} entries for N={N} sources")
+    CTFMNMF._expect(Y, (M, F, J), torch.complex64)
+    CTFMNMF._expect(T, (N, F, B), torch.float32)
+    CTFMNMF._expect(V, (N, B, J), torch.float32)
+    CTFMNMF._expect(logdet, (F,), torch.float64)
+    CTFMNMF._expect(out, (1,), torch.float64)
     st = stream if stream is not None else torch.cuda.current_stream()
+    dev = st.device
+    for t in (Y, T, V, logdet, out):
+        if not t.is_cuda or t.device != dev:
+            raise ValueError(f"every tensor must be on the stream's device {dev}, got {t.device}")
     ln_arr = (c_int * N)(*Ln)
     rc = lib().ctfmnmf_cost_noalloc(M, N, ln_arr, B, F, J, c_void_p(Y.data_ptr()), c_void_p(T.data_ptr()),
                                     c_void_p(V.data_ptr()), c_void_p(logdet.data_ptr()),

@@ -2,13 +2,17 @@
 // allocating device memory. The per-bin partial sums live in a fixed file-scope device
 // array instead of a buffer that a handle allocates.
 //
-// Why: some callers cannot call cudaMalloc at the point where they need the cost - code
-// running while a CUDA graph is being captured on its stream, code inside an allocator or
-// memory-pool callback, or a host application whose device memory is owned and budgeted
-// by another framework. They pass their own inputs and output; the scratch is ours.
+// Why: some callers cannot call cudaMalloc at the point where they need the cost - a
+// real-time audio thread (an allocation may synchronise the device and has no latency
+// bound), code inside an allocator or memory-pool callback (it would re-enter the
+// allocator), or a host application whose device memory is owned and budgeted by another
+// framework. They pass their own inputs and output; the scratch is ours.
 #include <stdio.h>
 
 #include <mutex>
+
+#include <cuda.h>   // CUresult and the context id type only: the function itself comes from
+                    // the runtime's driver entry-point query, so no link to libcuda
 
 #include "internal.cuh"
 
@@ -74,27 +78,53 @@ __global__ void noalloc_cost_sum(const int F, const double* __restrict__ scratch
     }
 }
 
-// Device address of the scratch array, looked up once per device (the array's name in
-// host code is only a host-side stand-in, not a device address).
+// Id of the context current on this thread (cuCtxGetId of the current context), 0 when none
+// is current or the query is unavailable. The id is unique for the life of the process, so
+// a device reset (a new primary context) shows up as a new id.
+static unsigned long long current_context_id()
+{
+    typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+    static CtxGetIdFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (CtxGetIdFn) nullptr;
+        }
+        return reinterpret_cast<CtxGetIdFn>(p);
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device (the array's name in host code
+// is only a host-side stand-in, not a device address). Looked up with cudaGetSymbolAddress
+// once per device and context: after a device reset the library's module is loaded again
+// and the array may move, so a new context id triggers a fresh lookup.
 static double* scratch_address(int* err)
 {
     static std::mutex mu;
     static double* addr[64] = {nullptr};
+    static unsigned long long ctx_of[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 64) {
         *err = e != cudaSuccess ? (int)e : (int)cudaErrorInvalidDevice;
         return nullptr;
     }
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || ctx == 0 || ctx != ctx_of[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_cost_scratch);
+        e = cudaGetSymbolAddress(&p, g_cost_scratch);     // makes the device's context current
         if (e != cudaSuccess) {
             *err = (int)e;
             return nullptr;
         }
         addr[dev] = static_cast<double*>(p);
+        ctx_of[dev] = current_context_id();
     }
     return addr[dev];
 }

@@ -143,3 +143,30 @@ def test_grad_form_rejects_bad_arguments_on_host(lib):
     assert lib.ctfmnmf_grad_launch_count(None, ctypes.byref(out)) == -1
     assert lib.ctfmnmf_grad_set_stream(None, None) == -1
     assert lib.ctfmnmf_grad_destroy(None) == 0
+
+
+def test_cost_noalloc_binding_checks_every_tensor_before_the_call():
+    """The no-allocation cost entry point trusts the sizes it is given, so its binding
+    rejects mismatched, mistyped or non-contiguous tensors with ValueError before any call
+    into the library (CPU tensors here: each case fails on its shape or type first)."""
+    import torch
+    M, N, F, J, B = 3, 2, 5, 16, 4
+    ok = dict(Y=torch.zeros((M, F, J), dtype=torch.complex64), T=torch.ones((N, F, B)),
+              V=torch.ones((N, B, J)), logdet=torch.zeros(F, dtype=torch.float64),
+              out=torch.zeros(1, dtype=torch.float64))
+    bad_cases = [
+        dict(V=torch.ones((N, B, J - 1))),                           # fewer frames than Y
+        dict(T=torch.ones((N, F - 1, B))),                           # fewer bins than Y
+        dict(logdet=torch.zeros(F - 1, dtype=torch.float64)),        # logdet too short
+        dict(logdet=torch.zeros(F, dtype=torch.float32)),            # logdet in float32
+        dict(out=torch.zeros(1, dtype=torch.float32)),               # out in float32
+        dict(out=torch.zeros(0, dtype=torch.float64)),               # out empty
+        dict(Y=torch.zeros((M, J, F), dtype=torch.complex64).transpose(1, 2)),   # not contiguous
+        dict(V=torch.ones((N, B, J), dtype=torch.float64)),          # V in float64
+    ]
+    for case in bad_cases:
+        args = dict(ok, **case)
+        with pytest.raises(ValueError):
+            api.cost_noalloc(args["Y"], args["T"], args["V"], args["logdet"], [2, 1], args["out"])
+    with pytest.raises(ValueError):
+        api.cost_noalloc(ok["Y"], ok["T"], ok["V"], ok["logdet"], [3], ok["out"])    # len(Ln) != N

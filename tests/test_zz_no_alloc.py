@@ -1,7 +1,8 @@
 """ctfmnmf_cost_noalloc against ctfmnmf_cost (GPU).
 
 The no-allocation entry point serves callers that cannot allocate device memory where they
-need the cost (for example while a CUDA graph is being captured). It must give the same
+need the cost (for example a real-time audio thread, where an allocation may synchronise
+the device, or code running inside an allocator callback). It must give the same
 negative log-likelihood as the handle-based ctfmnmf_cost, on consecutive calls that share
 its static scratch. Collected last on purpose, so that a run stopping at the first failure
 has run every other test before it.
