@@ -55,3 +55,41 @@ def cost_close(c_gpu, c_ref, tol, F, J, M):
     purely relative test is ill-conditioned; F*J*M is the number of terms of Eq. 5."""
     scale = max(abs(c_ref), float(F) * J * M)
     return abs(c_gpu - c_ref) <= tol * scale, abs(c_gpu - c_ref) / scale
+
+
+def per_bin_rel(a, b):
+    """Largest per-bin relative Frobenius error of rows [M][F][J] (bin = axis 1): a whole-tensor
+    norm dilutes one wrong bin among F, this does not."""
+    a, b = np.asarray(a), np.asarray(b)
+    num = np.sqrt(np.sum(np.abs(a - b) ** 2, axis=(0, 2)))
+    den = np.maximum(np.sqrt(np.sum(np.abs(b) ** 2, axis=(0, 2))), 1e-300)
+    return float(np.max(num / den))
+
+
+def per_bin_logdet(a, b):
+    """Largest per-bin |delta log|det W_i||, relative to max(1, |log|det W_i||)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b))))
+
+
+def expected_costs(name):
+    """Stored FP64 oracle costs of a full-size workload (tests/golden/expected_costs.json, written
+    by tests/golden/make_expected.py, which calls only the oracle), or a skip if absent."""
+    import json
+    import os
+    import pytest
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "expected_costs.json")
+    if not os.path.exists(path):
+        pytest.skip("expected_costs.json not generated")
+    with open(path) as f:
+        return json.load(f)["entries"][name]
+
+
+def check_fingerprint(entry, mix):
+    """The stored costs belong to this mixture: the generator still draws the same inputs (to
+    the last few bits, which numpy's elementary functions may round differently per platform)."""
+    fp = entry["fingerprint"]
+    got = {"x_power": float(np.sum(np.abs(mix.X.astype(np.complex128)) ** 2)),
+           "t0_sum": float(np.sum(mix.T0, dtype=np.float64)), "v0_sum": float(np.sum(mix.V0, dtype=np.float64))}
+    for k, v in fp.items():
+        assert abs(got[k] - v) <= 1e-9 * abs(v), (k, got[k], v)

@@ -76,3 +76,24 @@ def test_noise_level_matches_the_stated_snr():
     n = noisy.X.astype(np.complex128) - clean
     snr = 10 * np.log10(np.mean(np.abs(clean) ** 2) / np.mean(np.abs(n) ** 2))
     assert abs(snr - 30.0) < 0.5, snr
+
+
+def test_stored_oracle_costs_belong_to_the_generated_mixtures():
+    """tests/golden/expected_costs.json (written by tests/golden/make_expected.py from the
+    oracle) was made from the inputs this generator draws today: the fingerprint of every
+    stored mixture matches, and the stored C4 samples are the seeds the script picks."""
+    import importlib.util
+    import json
+    import os
+    from gpu_helpers import check_fingerprint
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "expected_costs.json")) as f:
+        entries = json.load(f)["entries"]
+    spec = importlib.util.spec_from_file_location("make_expected", os.path.join(here, "golden", "make_expected.py"))
+    me = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(me)
+    assert sorted(k for k in entries if k != "C3") == sorted(sp.name for sp in me.c4_samples())
+    specs = {sp.name: sp for sp in synth.batched_specs()}
+    for name, e in entries.items():
+        sp = synth.CONFIGS["C3"] if name == "C3" else specs[name]
+        check_fingerprint(e, synth.make_mixture(sp))
