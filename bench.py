@@ -58,6 +58,10 @@ def parse():
                    help="frames per thread of the two-kernel bin phase (0: the library's choice)")
     p.add_argument("--ip-steps", type=int, default=3,
                    help="timed steps of the ISS-vs-IP comparison on the plain workload (0 skips it)")
+    p.add_argument("--config-steps", type=int, default=3,
+                   help="timed steps of each other single-mixture workload, C1 C3 P4 P6 P8 (0 skips them)")
+    p.add_argument("--cpu-timings", type=int, default=1,
+                   help="1: time the FP64 oracle on further workloads and thread counts (about a minute)")
     return p.parse_args()
 
 
@@ -415,6 +419,117 @@ def longj_leg(args, peak):
             "iteration_roofline_frac": it_bytes * sp.iters / t / 1e9 / peak}
 
 
+def plain_config_leg(name, args, peak):
+    """One of the other single-mixture workloads (C1, C3 and the paper's Table I shapes
+    P4/P6/P8) on the path AUTO picks: CUDA events around ctfmnmf_iterate(iters) on the solver's
+    stream, median of the timed steps, L2 flushed between steps; the bin and frame phases timed
+    alone (event pair around each launch) for the kernel roofline; the whole iteration's
+    roofline from the graph-replayed rate."""
+    import torch
+    from paper_2510_02382_gb300 import synth
+    from paper_2510_02382_gb300.api import CTFMNMF
+    sp = synth.CONFIGS[name]
+    mix = synth.make_mixture(sp)
+    sv = CTFMNMF(sp.M, sp.N, sp.L, sp.B, sp.F, sp.J, Ln=mix.Ln)
+    X = torch.from_numpy(mix.X).cuda()
+    T0 = torch.from_numpy(mix.T0).cuda()
+    V0 = torch.from_numpy(mix.V0).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    st = sv.stream
+    ms = []
+    for k in range(args.config_steps + 1):
+        sv.load_stft(X)
+        sv.set_init(T0, V0)
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sv.iterate(sp.iters)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if k > 0:
+            ms.append(e0.elapsed_time(e1))
+    sv.load_stft(X)
+    sv.set_init(T0, V0)
+    sv.time_phases(3)
+    ms_bin, ms_frame = sv.time_phases(20)
+    path, shape = sv.path, sv.bin_shape()
+    sv.close()
+    t = statistics.median(ms) / 1000.0
+    M, N, F, J, B = sp.M, sp.N, sp.F, sp.J, sp.B
+    it_bytes = 16 * M * F * J + 8 * N * B * (F + J)
+    bin_bytes = 16 * M * F * J + 8 * N * B * F + 4 * N * B * J
+    bin_gbs = bin_bytes / (ms_bin * 1e-3) / 1e9
+    return {"workload": f"{name}: N={N} M={M} taps={tuple(mix.Ln)} F={F} J={J} B={B}, {sp.iters} iterations per step",
+            "steps": args.config_steps, "iterations_per_s": sp.iters / t, "bin_frames_per_s": F * J * sp.iters / t,
+            "path": path, "bin_shape": {"frames_per_thread": shape[0], "threads": shape[1]},
+            "kernel_times": {"bin_phase_ms": ms_bin, "frame_phase_ms": ms_frame},
+            "roofline": {"bound": "hbm", "kernel": "bin_phase_kernel", "achieved": bin_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": bin_gbs / peak, "algorithmic_bytes_per_launch": bin_bytes},
+            "iteration_roofline_frac": it_bytes * sp.iters / t / 1e9 / peak}
+
+
+def cpu_oracle_timings(seconds=6.0):
+    """The FP64 oracle, as it stands, on the host cores in the same run, beside the GPU numbers
+    (a reported baseline, not the target): C2 with one thread and with every core, C3 with the
+    ISS and with the IP update, and the batched workload as 4 of its mixtures x 5 iterations,
+    extrapolated linearly in the sum of F*J*iterations over all 64 mixtures and 50 iterations.
+    Each timing is a bounded sample of iterations (at least 2, until about `seconds`)."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+from paper_2510_02382_gb300 import synth
+from oracle import ctfmnmf_oracle as O
+
+def rate(spec, update, seconds):
+    mix = synth.make_mixture(spec)
+    x, W, b, v = O.init_state(mix.X, mix.T0, mix.V0)
+    n, t0 = 0, time.perf_counter()
+    while n < 2 or time.perf_counter() - t0 < seconds:
+        W, b, v, y = O.iterate(x, W, b, v, mix.Ln, update=update)
+        n += 1
+    return n, time.perf_counter() - t0
+
+out = {{}}
+for name, upd in (("C2", "iss"), ("C3", "iss"), ("C3", "ip")):
+    n, dt = rate(synth.CONFIGS[name], upd, {seconds})
+    out[name + "_" + upd] = {{"iterations": n, "seconds": dt, "iterations_per_s": n / dt}}
+specs = synth.batched_specs()
+picks = [specs[k] for k in (0, 21, 42, 63)]
+t = 0.0
+for sp in picks:
+    mix = synth.make_mixture(sp)
+    x, W, b, v = O.init_state(mix.X, mix.T0, mix.V0)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        W, b, v, y = O.iterate(x, W, b, v, mix.Ln)
+    t += time.perf_counter() - t0
+work_sample = sum(sp.F * sp.J * 5 for sp in picks)
+work_all = sum(sp.F * sp.J * sp.iters for sp in specs)
+out["C4"] = {{"sample": "mixtures 0, 21, 42, 63 x 5 iterations", "seconds": t,
+             "extrapolated_seconds_per_50_iterations": t * work_all / work_sample,
+             "batch_iterations_per_s": specs[0].iters / (t * work_all / work_sample)}}
+print(json.dumps(out))
+"""
+    ncores = os.cpu_count() or 1
+    res = {"nproc": ncores}
+    for label, threads in (("one_thread", 1), ("all_cores", ncores)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+                   MKL_NUM_THREADS=str(threads))
+        if label == "all_cores":       # only C2 is rerun with every core
+            c = code.replace('(("C2", "iss"), ("C3", "iss"), ("C3", "ip"))', '(("C2", "iss"),)')
+            c = c[:c.index("specs = synth.batched_specs()")] + "print(json.dumps(out))\n"
+        else:
+            c = code
+        r = subprocess.run([sys.executable, "-c", c], capture_output=True, text=True, env=env, timeout=900)
+        if r.returncode != 0:
+            res[label] = {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+            continue
+        res[label] = json.loads(r.stdout.strip().splitlines()[-1])
+        res[label]["threads"] = threads
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_2510_02382_gb300 import synth
@@ -524,6 +639,17 @@ def run_ours(args):
         phase = {"bin_phase_ms": ms_bin, "frame_phase_ms": ms_frame}
     peak, peak_src = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9
+    # the kernels inside the replayed graph: the timed step's time per iteration (a step also
+    # loads the STFT and the init, about 1 % here), split between the phases in the ratio of
+    # their isolated launch times (an estimate: events cannot sit inside a graph)
+    it_us = 1000.0 * (total_ms / args.steps) / iters
+    if solver.path == "persistent":
+        in_graph = {"iteration_us": it_us}
+    else:
+        share = ms_bin / (ms_bin + ms_frame)
+        in_graph = {"iteration_us": it_us, "bin_phase_us_est": share * it_us, "frame_phase_us_est": (1 - share) * it_us,
+                    "bin_phase_frac_est": kbytes / (share * it_us * 1e-6) / 1e9 / peak if kname == "bin_phase_kernel" else None,
+                    "method": "timed step per iteration, split by the ratio of the isolated launch times"}
     traffic = captured_traffic(kname, iters if kname == "persistent_kernel" else 1,
                                100 if kname == "persistent_kernel" else 1)
     # arithmetic view: about 23 M^2 (ISS) + 12 N B (NMF) flops per bin-frame and iteration
@@ -536,12 +662,15 @@ def run_ours(args):
     fwdbwd = fwd_bwd_leg(args, peak) if args.fwdbwd_steps > 0 else None
     ipcmp = ip_leg(args, spec, iters) if args.ip_steps > 0 else None
     longj = longj_leg(args, peak) if args.longj_steps > 0 else None
+    configs = ({name: plain_config_leg(name, args, peak) for name in ("C1", "C3", "P4", "P6", "P8")}
+               if args.config_steps > 0 else None)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     cpu = cpu_baseline_sample() if world == 1 else None
+    cpu_more = cpu_oracle_timings() if (world == 1 and args.cpu_timings) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -553,7 +682,9 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
                      "alu": {"achieved_tflops": flops / (kms * 1e-3) / 1e12, "peak_tflops": fp32_peak,
-                             "frac": flops / (kms * 1e-3) / 1e12 / fp32_peak}},
+                             "peak_source": "nominal, not measured: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
+                             "frac": flops / (kms * 1e-3) / 1e12 / fp32_peak},
+                     "in_graph": in_graph},
         "path": solver_path,
         "bin_shape": {"frames_per_thread": bin_fpt, "threads": bin_nt},
         "kernel_times": phase,
@@ -566,6 +697,8 @@ def run_ours(args):
         "fwd_bwd": fwdbwd,
         "iss_vs_ip": ipcmp,
         "long_j": longj,
+        "plain_configs": configs,
+        "cpu_oracle_timings": cpu_more,
     }
     if batched is not None:
         batched["vs_plain_bin_frames"] = batched["bin_frames_per_s"] / line["bin_frames_per_s"]

@@ -48,7 +48,9 @@ typedef enum ctfmnmf_status {
     CTFMNMF_ENONFINITE = -4,   /* the input STFT or NMF factors hold NaN or Inf          */
     CTFMNMF_ETIMEOUT = -5,     /* a bounded device-side wait gave up                     */
     CTFMNMF_ENOMEM = -6,       /* device allocation failed                                */
-    CTFMNMF_EUNSUPPORTED = -7  /* valid shape that these kernels do not handle (see create) */
+    CTFMNMF_EUNSUPPORTED = -7, /* valid shape that these kernels do not handle (see create) */
+    CTFMNMF_EBOUNDS = -8       /* a device-side bounds check of a CTFMNMF_DEBUG build stopped
+                                  a thread block before an out-of-range access             */
 } ctfmnmf_status;
 
 /* Activation update variants (Eq. 18). */
@@ -82,6 +84,17 @@ typedef struct ctfmnmf_options {
                                   or 8 (M <= 4) when it fits J; 0 (default): with path
                                   AUTO timed among the candidates, else the fewest that
                                   fit. EUNSUPPORTED if the value cannot run this shape  */
+    float eps_floor;           /* floor of T and V after each multiplicative update and at
+                                  set_init; 0 (default) = 1e-12. Must be >= 0 and finite  */
+    int deterministic_reduce;  /* 1 (default): every reduction in a fixed order, so that a
+                                  run repeats bit for bit; 0: the long-J cluster bin phase
+                                  may add its row powers with shared-memory atomics      */
+    int check_finite;          /* 1: scan Y, T and V for NaN/Inf after every iteration of
+                                  the two-kernel path (after the whole call on the
+                                  persistent path); the next synchronising call returns
+                                  CTFMNMF_ENONFINITE and the state must be reloaded.
+                                  0 (default): no scan. Builds made with -DCTFMNMF_DEBUG
+                                  always scan                                            */
     int reserved[1];           /* must be zero                                          */
 } ctfmnmf_options;
 
@@ -398,6 +411,18 @@ int ctfmnmf_time_persistent(ctfmnmf_t h, int n_iter, double* ms);
  * CTFMNMF_ETIMEOUT and the state must be reloaded (ctfmnmf_load_stft). cta < 0 clears it.
  */
 int ctfmnmf_debug_skip_arrival(ctfmnmf_t h, int cta);
+
+/*
+ * Debug builds (compiled with -DCTFMNMF_DEBUG): every kernel checks the indices it takes from
+ * its launch (bin, frame tile, the batched form's work lists) against the shape before any
+ * memory access; a failed check records itself in a device status word and the block returns,
+ * and the next synchronising call on an affected handle returns CTFMNMF_EBOUNDS. This test hook
+ * overwrites entry `entry` of bin class `cls`'s work list of batch b with (mixture, bin) so that
+ * a test can watch such a check stop a block. Release builds return CTFMNMF_EUNSUPPORTED and
+ * change nothing (their kernels do not check). *is_debug (host, may be NULL) receives 1 in a
+ * debug build, else 0.
+ */
+int ctfmnmf_debug_set_work(ctfmnmf_batch_t b, int cls, int entry, int mixture, int bin, int* is_debug);
 
 #ifdef __cplusplus
 }

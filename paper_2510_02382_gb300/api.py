@@ -16,7 +16,7 @@ from .build import lib_path
 c_int, c_void_p, c_double, c_char_p = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_char_p
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ESTATE", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
-          -6: "ENOMEM", -7: "EUNSUPPORTED"}
+          -6: "ENOMEM", -7: "EUNSUPPORTED", -8: "EBOUNDS"}
 V_ALL_TAPS, V_TAP0 = 0, 1
 W_ISS, W_IP = 0, 1
 
@@ -27,7 +27,8 @@ class Dims(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("v_update", c_int), ("normalize", c_int), ("use_graph", c_int), ("path", c_int),
-                ("wait_timeout_ms", c_int), ("w_update", c_int), ("bin_fpt", c_int), ("reserved", c_int * 1)]
+                ("wait_timeout_ms", c_int), ("w_update", c_int), ("bin_fpt", c_int), ("eps_floor", ctypes.c_float),
+                ("deterministic_reduce", c_int), ("check_finite", c_int), ("reserved", c_int * 1)]
 
 
 PATHS = {"auto": 0, "two_kernel": 1, "persistent": 2}
@@ -69,6 +70,7 @@ _SIGS = {
     "ctfmnmf_get_bin_shape": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ctfmnmf_time_persistent": (c_int, [c_void_p, c_int, c_void_p]),
     "ctfmnmf_debug_skip_arrival": (c_int, [c_void_p, c_int]),
+    "ctfmnmf_debug_set_work": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
     "ctfmnmf_cost_noalloc": (c_int, [c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     "ctfmnmf_batch_create": (c_int, [c_int, c_void_p, c_void_p]),
@@ -90,10 +92,12 @@ _SIGS = {
 
 
 def lib():
-    """Load libctfmnmf.so (raises if it has not been built)."""
+    """Load libctfmnmf.so (raises if it has not been built). With CTFMNMF_DEBUG_BUILD=1 in the
+    environment, the CTFMNMF_DEBUG build (device bounds checks, NaN/Inf scan every iteration)
+    is loaded instead."""
     global _LIB
     if _LIB is None:
-        p = lib_path()
+        p = lib_path(debug=os.environ.get("CTFMNMF_DEBUG_BUILD") == "1")
         if not os.path.exists(p):
             raise RuntimeError(f"{p} is missing: build it with `python -m paper_2510_02382_gb300.build`")
         L = ctypes.CDLL(p)
@@ -154,6 +158,13 @@ class Batch:
         offs = (ctypes.c_longlong * len(self.solvers))(*[int(o) for o in offsets])
         _check(lib().ctfmnmf_batch_get_separated(self._h, c_void_p(C.data_ptr()), offs), None)
         return C
+
+    def debug_set_work(self, cls: int, entry: int, mixture: int, bin_: int) -> bool:
+        """Test hook of CTFMNMF_DEBUG builds (ctfmnmf_debug_set_work); returns whether the loaded
+        library is a debug build (a release build raises EUNSUPPORTED and changes nothing)."""
+        dbg = c_int(0)
+        _check(lib().ctfmnmf_debug_set_work(self._h, int(cls), int(entry), int(mixture), int(bin_), ctypes.byref(dbg)), None)
+        return bool(dbg.value)
 
     def info(self):
         out = (c_int * 5)()
@@ -290,7 +301,8 @@ class CTFMNMF:
     def __init__(self, M: int, N: int, L: int, B: int, F: int, J: int,
                  Ln: Optional[Sequence[int]] = None, v_update: str = "all_taps",
                  normalize: bool = True, use_graph: bool = True, path: str = "auto",
-                 wait_timeout_ms: int = 0, w_update: str = "iss", bin_fpt: int = 0, stream=None):
+                 wait_timeout_ms: int = 0, w_update: str = "iss", bin_fpt: int = 0, eps_floor: float = 0.0,
+                 deterministic_reduce: bool = True, check_finite: bool = False, stream=None):
         import torch
         self.M, self.N, self.L, self.B, self.F, self.J = M, N, L, B, F, J
         d = Dims(M, N, L, B, F, J)
@@ -303,6 +315,9 @@ class CTFMNMF:
         o.wait_timeout_ms = int(wait_timeout_ms)
         o.w_update = {"iss": W_ISS, "ip": W_IP}[w_update]
         o.bin_fpt = int(bin_fpt)
+        o.eps_floor = float(eps_floor)
+        o.deterministic_reduce = int(bool(deterministic_reduce))
+        o.check_finite = int(bool(check_finite))
         ln_arr = (c_int * N)(*Ln) if Ln is not None else None
         h = c_void_p()
         rc = lib().ctfmnmf_create_ex(ctypes.byref(d), ln_arr, ctypes.byref(o), ctypes.byref(h))

@@ -29,8 +29,13 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def lib_path() -> str:
-    return os.path.join(OUT_DIR, LIB_NAME)
+DEBUG_DIR = os.path.join(PKG, "_build_debug")
+
+
+def lib_path(debug: bool = False) -> str:
+    """The release library, or (debug) the CTFMNMF_DEBUG build with device bounds checks and a
+    NaN/Inf scan after every iteration."""
+    return os.path.join(DEBUG_DIR if debug else OUT_DIR, LIB_NAME)
 
 
 def is_stale() -> bool:
@@ -48,13 +53,16 @@ def _flags(extra=()):
                    "-I", os.path.join(ROOT, "include"), *extra]
 
 
-def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, ptxas_verbose: bool = False, debug: bool = False) -> str:
+    out_dir = DEBUG_DIR if debug else OUT_DIR
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = nvcc_path()
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+    if debug:
+        extra.append("-DCTFMNMF_DEBUG")
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd += ["-x", "cu"]
@@ -66,16 +74,16 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(compile_one, SOURCES))
     logs = "".join(r[1] for r in results)
-    tmp = lib_path() + ".tmp"
+    tmp = lib_path(debug) + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[r[0] for r in results]]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, lib_path())
+    os.replace(tmp, lib_path(debug))
     if verbose or ptxas_verbose:
         sys.stdout.write(logs)
-    return lib_path()
+    return lib_path(debug)
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, ptxas_verbose="-v" in sys.argv))
+    print(build(verbose=True, ptxas_verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -61,17 +61,21 @@ int check_flag(ctfmnmf* h, int mask, const char* what)
 
 using ctf::kFinalizeKernels;
 
-// Synchronise the stream and report a device wait that ran out (then clear the report).
+// Synchronise the stream and report what the device recorded since the last report (then
+// clear it): flag[1] a bounded wait ran out, flag[2] the NaN/Inf scan found a non-finite value,
+// flag[3] a bounds check of a debug build stopped a block. The state is unusable after any.
 int sync_and_check(ctfmnmf* h)
 {
-    int flag = 0;
-    CUDA_TRY(h, cudaMemcpyAsync(&flag, h->d.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    int flag[3] = {0, 0, 0};
+    CUDA_TRY(h, cudaMemcpyAsync(flag, h->d.flag + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    if (flag) {
-        CUDA_TRY(h, cudaMemsetAsync(h->d.flag + 1, 0, sizeof(int), h->stream));
+    if (flag[0] || flag[1] || flag[2]) {
+        CUDA_TRY(h, cudaMemsetAsync(h->d.flag + 1, 0, 3 * sizeof(int), h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         h->loaded = false;
-        return fail(h, CTFMNMF_ETIMEOUT, "a device-side wait of the persistent kernel ran out");
+        if (flag[2]) return fail(h, CTFMNMF_EBOUNDS, "a device-side bounds check stopped a thread block");
+        if (flag[0]) return fail(h, CTFMNMF_ETIMEOUT, "a device-side wait of the persistent kernel ran out");
+        return fail(h, CTFMNMF_ENONFINITE, "the state holds NaN or Inf after an iteration");
     }
     return CTFMNMF_OK;
 }
@@ -85,6 +89,7 @@ int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
                        : h->cplan.ok ? ctf::launch_cluster_bin_phase(h->s, h->d, tap0, h->cplan, st)
                                      : ctf::launch_bin_phase_as(h->s, h->d, tap0, h->bin_fpt, h->bin_nt, st));
         CUDA_TRY(h, ctf::launch_frame_phase(h->s, h->d, tap0, h->opt.normalize, st));
+        if (h->opt.check_finite) CUDA_TRY(h, ctf::launch_finite_scan(h->s, h->d, st));
     }
     CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, st));
     return CTFMNMF_OK;
@@ -92,7 +97,7 @@ int enqueue_iterations(ctfmnmf* h, int n_iter, cudaStream_t st)
 
 }  // namespace
 
-long long ctf::iteration_kernels(int n_iter) { return 2LL * n_iter + kFinalizeKernels; }
+long long ctf::iteration_kernels(int n_iter, bool scan) { return (scan ? 3LL : 2LL) * n_iter + kFinalizeKernels; }
 
 namespace {
 using ctf::iteration_kernels;
@@ -113,6 +118,7 @@ void ctfmnmf_default_options(ctfmnmf_options* opt)
     opt->v_update = CTFMNMF_V_ALL_TAPS;
     opt->normalize = 1;
     opt->use_graph = 1;
+    opt->deterministic_reduce = 1;
 }
 
 // AUTO: time a few iterations of each candidate on a probe state and keep the fastest — the
@@ -221,12 +227,22 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         if (o.reserved[0]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
         if (o.bin_fpt != 0 && o.bin_fpt != 1 && o.bin_fpt != 2 && o.bin_fpt != 4 && o.bin_fpt != 8)
             return fail(nullptr, CTFMNMF_EINVAL, "bin_fpt must be 0, 1, 2, 4 or 8");
+        if (!(o.eps_floor >= 0.f) || !(o.eps_floor < 3.0e38f))
+            return fail(nullptr, CTFMNMF_EINVAL, "eps_floor must be finite and >= 0");
+        if ((o.deterministic_reduce != 0 && o.deterministic_reduce != 1) || (o.check_finite != 0 && o.check_finite != 1))
+            return fail(nullptr, CTFMNMF_EINVAL, "deterministic_reduce and check_finite must be 0 or 1");
     }
+#ifdef CTFMNMF_DEBUG
+    o.check_finite = 1;                            // debug builds always scan for NaN/Inf
+#endif
     Shape s;
     memset(&s, 0, sizeof(s));
     s.M = M; s.N = N; s.B = B; s.F = F; s.J = J;
     s.Jp = (J + 7) / 8 * 8;
     s.FBp = (F * B + 3) / 4 * 4;
+    s.invJ = 1.0 / (double)J;
+    s.floor_nmf = o.eps_floor > 0.f ? o.eps_floor : ctf::kFloorNmf;
+    s.det_reduce = o.deterministic_reduce;
     int total = 0, lmax = 0;
     for (int n = 0; n < N; ++n) {
         const int t = Ln ? Ln[n] : M / N + (n < M % N ? 1 : 0);
@@ -283,7 +299,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         {(void**)&d.V, sizeof(float) * (size_t)N * B * s.Jp},
         {(void**)&d.invlam, sizeof(float) * FNJ},
         {(void**)&d.P, sizeof(float) * FNJ},
-        {(void**)&d.mupart, sizeof(float) * MF},
+        {(void**)&d.mupart, sizeof(double) * MF},
         {(void**)&d.scale, sizeof(float) * CTFMNMF_MAX_M},
         {(void**)&d.flag, sizeof(int) * 4},
         {(void**)&d.cost_part, sizeof(double) * F},
@@ -310,7 +326,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     if (rc == CTFMNMF_OK && (cudaMemset(d.flag, 0, sizeof(int) * 4) != cudaSuccess ||
                              cudaMemset(d.sync, 0, sizeof(unsigned) * 32) != cudaSuccess ||
                              cudaMemset(d.P, 0, sizeof(float) * FNJ) != cudaSuccess ||
-                             cudaMemset(d.mupart, 0, sizeof(float) * MF) != cudaSuccess))
+                             cudaMemset(d.mupart, 0, sizeof(double) * MF) != cudaSuccess))
         rc = CTFMNMF_ECUDA;
     if (rc == CTFMNMF_OK && !one_block) {
         h->cplan = ctf::plan_cluster(s);
@@ -464,11 +480,15 @@ int ctfmnmf_iterate(ctfmnmf_t h, int n_iter)
         h->skip_cta = -1;
         CUDA_TRY(h, ctf::launch_finalize(h->s, h->d, h->stream));
         h->launches += 1 + kFinalizeKernels;
+        if (h->opt.check_finite) {
+            CUDA_TRY(h, ctf::launch_finite_scan(h->s, h->d, h->stream));
+            h->launches += 1;
+        }
         return CTFMNMF_OK;
     }
     if (!h->opt.use_graph) {
         const int rc = enqueue_iterations(h, n_iter, h->stream);
-        if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter);
+        if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter, h->opt.check_finite != 0);
         return rc;
     }
     if (!h->graph || h->graph_iters != n_iter) {
@@ -494,7 +514,7 @@ int ctfmnmf_iterate(ctfmnmf_t h, int n_iter)
         h->graph_iters = n_iter;
     }
     CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
-    h->launches += iteration_kernels(n_iter);
+    h->launches += iteration_kernels(n_iter, h->opt.check_finite != 0);
     return CTFMNMF_OK;
 }
 
@@ -614,7 +634,7 @@ int ctfmnmf_time_phases(ctfmnmf_t h, int n_iter, double* ms)
     }
     if (rc == CTFMNMF_OK && ctf::launch_finalize(h->s, h->d, h->stream) != cudaSuccess)
         rc = fail(h, CTFMNMF_ECUDA, "finalize launch failed");
-    if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter);
+    if (rc == CTFMNMF_OK) h->launches += iteration_kernels(n_iter, false);
     for (auto& e : ev) cudaEventDestroy(e);
     if (rc != CTFMNMF_OK) return rc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));

@@ -28,7 +28,9 @@ cudaError_t batch_bin_m8(int fpt, int kb, const MixDesc* mixes, const int2* work
 constexpr int kBatchFrameThreads = 256;
 constexpr int kBatchFrameSmemBytes = 48 * 1024;
 
-// EXACT: every mixture of the launch has B equal to the class width BB.
+// EXACT: every mixture of the launch has B equal to the class width BB. A work item
+// (mixture, -1) forms that mixture's normalisation scale of this iteration (FP64, Eq. 19)
+// and stores it as its pending scale; every other item is one (8-frame tile, source).
 template <int BB, bool EXACT>
 __global__ void __launch_bounds__(kBatchFrameThreads, frame_min_blocks<BB>())
 batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ work, const int v_tap0,
@@ -36,8 +38,6 @@ batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ w
 {
     extern __shared__ float4 fsm4[];
     __shared__ MixDesc md;
-    __shared__ float s_scale[CTFMNMF_MAX_M];
-    __shared__ float red_cta[(kBatchFrameThreads / 32) * CTFMNMF_MAX_M];
     const int2 w = work[blockIdx.x];                   // (mixture, item)
     {
         const int* src = reinterpret_cast<const int*>(mixes + w.x);
@@ -47,15 +47,23 @@ batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ w
     __syncthreads();
     const Shape& s = md.s;
     const State& d = md.d;
+#ifdef CTFMNMF_DEBUG
+    if (w.y < -1 || w.y >= (s.Jp / kFrameTile) * s.N) {   // an item outside the mixture
+        if (threadIdx.x == 0) atomicOr(d.flag + 3, 1);
+        return;
+    }
+#endif
+    if (w.y < 0) {
+        scales_fp64(s, d, normalize, reinterpret_cast<double*>(fsm4));
+        return;
+    }
     const Grp g{(int)threadIdx.x, kBatchFrameThreads, 0};
     const int fixed = frame_smem_fixed<BB>(kBatchFrameThreads);
     const int FC = frame_chunk(kBatchFrameSmemBytes / 4, s.B, fixed);
-    const ScaleJob job{s_scale, red_cta, normalize};
     if constexpr (BB <= 16)
-        frame_item<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+        frame_item<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
     else
-        frame_item_wide<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
-    if (w.y == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
+        frame_item_wide<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
 }
 
 // ---------------------------------------------------------------- dispatch

@@ -105,6 +105,7 @@ int make_plan(const std::vector<ctfmnmf*>& hs, int pref, bool merge, Plan* out)
         if (ctf::batch_frame_chunk(s.B, BB) < 4) return CTFMNMF_EUNSUPPORTED;
         const int items = (s.Jp / 8) * s.N;
         const int key = 2 * BB + (s.B == BB ? 1 : 0);     // mixtures whose B is the class width apart
+        fwork[key].push_back(make_int2((int)b, -1));       // the mixture's normalisation scale
         for (int it = 0; it < items; ++it) fwork[key].push_back(make_int2((int)b, it));
     }
     for (auto& kv : fwork) {
@@ -426,6 +427,34 @@ int ctfmnmf_batch_info(ctfmnmf_batch_t b, int* info)
     info[3] = b->policy;
     info[4] = (int)(b->launches & 0x7fffffff);
     return CTFMNMF_OK;
+}
+
+int ctfmnmf_debug_set_work(ctfmnmf_batch_t b, int cls, int entry, int mixture, int bin, int* is_debug)
+{
+    ctf::set_thread_error("");
+#ifdef CTFMNMF_DEBUG
+    if (is_debug) *is_debug = 1;
+#else
+    if (is_debug) *is_debug = 0;
+#endif
+    if (!b) return fail_b(CTFMNMF_EINVAL, "batch is NULL");
+    if (cls < 0 || cls >= (int)b->plan.bins.size()) return fail_b(CTFMNMF_EINVAL, "no such bin class");
+    const BatchClass& c = b->plan.bins[cls];
+    if (entry < 0 || entry >= c.blocks) return fail_b(CTFMNMF_EINVAL, "no such entry in the bin class");
+    if (mixture < 0 || mixture >= (int)b->hs.size()) return fail_b(CTFMNMF_EINVAL, "no such mixture");
+#ifdef CTFMNMF_DEBUG
+    const int2 w = make_int2(mixture, bin);
+    cudaStream_t st = b->hs[0]->stream;
+    if (cudaMemcpyAsync(c.work + entry, &w, sizeof(int2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        return fail_b(CTFMNMF_ECUDA, "work-list write failed: %s", cudaGetErrorString(e));
+    }
+    return CTFMNMF_OK;
+#else
+    (void)bin;
+    return fail_b(CTFMNMF_EUNSUPPORTED, "work lists can be changed only in a CTFMNMF_DEBUG build");
+#endif
 }
 
 int ctfmnmf_batch_load_stft(ctfmnmf_batch_t b, const void* X, const long long* offsets)

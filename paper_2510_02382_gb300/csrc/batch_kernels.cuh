@@ -24,6 +24,12 @@ batch_bin_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ wor
     __syncthreads();
     const Shape& s = md.s;
     const State& d = md.d;
+#ifdef CTFMNMF_DEBUG
+    if (w.y < 0 || w.y >= s.F) {                       // a bin outside the mixture: report, touch nothing
+        if (threadIdx.x == 0) atomicOr(d.flag + 3, 1);
+        return;
+    }
+#endif
     const int i = w.y;
     const Grp g{(int)threadIdx.x, (int)blockDim.x, 0};
     float2 y[M][FPT];

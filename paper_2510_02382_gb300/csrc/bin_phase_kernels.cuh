@@ -15,6 +15,12 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
     float* smem = reinterpret_cast<float*>(smem4);
     __shared__ float s_scale[CTFMNMF_MAX_M];
     const int i = blockIdx.x;
+#ifdef CTFMNMF_DEBUG
+    if (i >= s.F || (int)blockDim.x * FPT < s.J) {     // a bin or a frame outside the launch
+        if (threadIdx.x == 0) atomicOr(d.flag + 3, 1);
+        return;
+    }
+#endif
     const Grp g{(int)threadIdx.x, (int)blockDim.x, 0};
     float2 y[M][FPT];
     float2 wcol[M];

@@ -61,8 +61,13 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
     __shared__ float red[16][32];
     __shared__ float tot[32];
     __shared__ float s_scale[CTFMNMF_MAX_M];
+    __shared__ float s_fac[CTFMNMF_MAX_M];          // per source: mu_{(n,0)}^2 for the stored 1/lambda
 
     if (tid < CTFMNMF_MAX_M) s_scale[tid] = tid < M ? d.scale[tid] : 1.f;
+    if (tid < N) {
+        const float s0 = d.scale[s.row0[tid]];
+        s_fac[tid] = 1.0f / (s0 * s0);
+    }
     for (int t = tid; t < 2 * N * B + M; t += NT) acc[t] = 0.f;
     __syncthreads();
 
@@ -87,13 +92,16 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
                 v = make_float2(v.x * s_scale[r], v.y * s_scale[r]);
             }
             y[r][f] = v;
-            if (kPhiReg) phi[r % PR][f % PF] = (jl < Jc && j < J && j >= l) ? __ldcg(il + (size_t)n * Jp + j - l) : 0.f;
+            if (kPhiReg)
+                phi[r % PR][f % PF] =
+                    (jl < Jc && j < J && j >= l) ? scaled_invlam(__ldcg(il + (size_t)n * Jp + j - l), s_fac[n]) : 0.f;
         }
     }
     auto phi_at = [&](int p, int f) -> float {
         if (kPhiReg) return phi[p % PR][f % PF];
         const int jl = tid + f * NT, j = j0 + jl, l = s.row_l[p];
-        return (jl < Jc && j < J && j >= l) ? __ldg(il + (size_t)s.row_n[p] * Jp + j - l) : 0.f;
+        const int n = s.row_n[p];
+        return (jl < Jc && j < J && j >= l) ? scaled_invlam(__ldg(il + (size_t)n * Jp + j - l), s_fac[n]) : 0.f;
     };
     float2 wcol[M];                                 // threads < M: column tid of W_i
     if (tid < M) {
@@ -104,8 +112,9 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
         }
     }
 
-    // ---- ISS sweep (Eqs. 11-16) with cluster-wide sums
-    const float invJ = 1.0f / (float)J;
+    // ---- ISS sweep (Eqs. 11-16) with cluster-wide sums; the normaliser of row r (FP64) is
+    //      applied after the sweep, as in bin_body (every later step is homogeneous in row r)
+    __shared__ float s_scr[CTFMNMF_MAX_M];
     float detf = 1.0f;
 #pragma unroll
     for (int r = 0; r < M; ++r) {
@@ -160,9 +169,7 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
                 z[p] = make_float2(tot[c] / tot[p], tot[c + 1] / tot[p]);
             }
         }
-        const float qv = tot[r] * invJ;
-        const float sc = qv > 0.f ? 1.0f / sqrtf(qv) : 1.0f;
-        detf *= sc;
+        if (tid == 0) s_scr[r] = tot[r];            // the sum J q_r, inverted after the sweep
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const float2 yr = y[r][f];
@@ -172,7 +179,6 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
                 y[p][f].x -= z[p].x * yr.x - z[p].y * yr.y;
                 y[p][f].y -= z[p].x * yr.y + z[p].y * yr.x;
             }
-            y[r][f] = make_float2(yr.x * sc, yr.y * sc);
         }
         if (tid < M) {
             const float2 wr = wcol[r];
@@ -182,8 +188,22 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
                 wcol[p].x -= z[p].x * wr.x - z[p].y * wr.y;
                 wcol[p].y -= z[p].x * wr.y + z[p].y * wr.x;
             }
-            wcol[r] = make_float2(wr.x * sc, wr.y * sc);
         }
+    }
+    if (warp == 0) {                                // FP64 normalisers, one row per lane of warp 0
+        __syncwarp();
+        const float sc = iss_normaliser(lane < M ? s_scr[lane] : 0.f, s.invJ);
+        __syncwarp();
+        if (lane < M) s_scr[lane] = sc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        const float sc = s_scr[r];
+        detf *= sc;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) y[r][f] = make_float2(y[r][f].x * sc, y[r][f].y * sc);
+        if (tid < M) wcol[r] = make_float2(wcol[r].x * sc, wcol[r].y * sc);
     }
 
     // ---- rows out, |y|^2 for the delayed power, row-power partials
@@ -203,9 +223,17 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
             }
         }
         const float v = warp_sum(rp[r]);
-        if (lane == 0) atomicAdd(&rpw[r], v);
+        if (lane == 0) {                            // fixed order (below), or shared atomics
+            if (s.det_reduce) red[warp][r] = v;
+            else atomicAdd(&rpw[r], v);
+        }
     }
     cl.sync();                                      // every block's |y|^2 is in place
+    if (s.det_reduce && tid < M) {
+        float t = 0.f;
+        for (int w = 0; w < NW; ++w) t += red[w][tid];
+        rpw[tid] = t;
+    }
 
     // ---- delayed power P_n(j) = sum_{l < L_n, j + l < J} |y_{(n,l)}(j + l)|^2 (the next
     //      block's first frames past this chunk's end), basis-MU weights A = P / lambda^2 and
@@ -215,7 +243,7 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
 #pragma unroll 4
     for (int e = tid; e < N * Jc; e += NT) {
         const int n = e / Jc, jl = e - n * Jc, j = j0 + jl;
-        const float w = j < J ? __ldcg(il + (size_t)n * Jp + j) : 0.f;     // 1/lambda_{n,i,j}
+        const float w = j < J ? scaled_invlam(__ldcg(il + (size_t)n * Jp + j), s_fac[n]) : 0.f;   // 1/lambda_{n,i,j}
         const int r0 = s.row0[n], lq = min(s.Ln[n], J - j);            // taps l with j + l < J
         float P = 0.f;
         for (int l = 0; l < lq; ++l) {
@@ -265,11 +293,11 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
             float* Tp = d.T + (size_t)n * s.FBp + (size_t)i * B + k;
             const float tcur = __ldcg(Tp) * (s0 * s0);
             const float tn = (den > 0.f) ? tcur * sqrtf(num / den) : tcur;
-            __stcg(Tp, fmaxf(tn, kFloorNmf));
+            __stcg(Tp, fmaxf(tn, s.floor_nmf));
         }
         if (tid < M) {
-            float t = 0.f;
-            for (int b = 0; b < CL; ++b) t += cl.map_shared_rank(rpw, b)[tid];
+            double t = 0.0;                         // the bin's row power in FP64 (Eq. 19)
+            for (int b = 0; b < CL; ++b) t += (double)cl.map_shared_rank(rpw, b)[tid];
             __stcg(d.mupart + (size_t)i * M + tid, t);
 #pragma unroll
             for (int p = 0; p < M; ++p) __stcg(d.W + ((size_t)i * M + p) * M + tid, wcol[p]);

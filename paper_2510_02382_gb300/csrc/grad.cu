@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kGradTile) grad_vmu_kernel(const Shape s, cons
         if (live) {
             const float g1 = g.gV[gin][idx];
             const float V1 = nxt.V[((size_t)n * B + k) * Jp + j], V = v[k];
-            if (V1 > kFloorNmf && V > 0.f && den[k] > 0.f) {
+            if (V1 > s.floor_nmf && V > 0.f && den[k] > 0.f) {
                 // V1 = V R, R = sqrt(numV / denV): dR/dnum = 1/(2 R den), dR/dden = -R/(2 den)
                 const float R = V1 / V, gR = g1 * V;
                 gn = gR / (2.f * R * den[k]);
@@ -330,7 +330,7 @@ __global__ void grad_inputs_kernel(const Shape s, const StatePtrs* __restrict__ 
         for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
             const int n = t / B, k = t - n * B;
             const size_t o = (size_t)n * FBp + (size_t)i * B + k;
-            gT0[(((size_t)sm * N + n) * F + i) * B + k] = in.T[o] > kFloorNmf ? g.gT[(size_t)sm * N * FBp + o] : 0.f;
+            gT0[(((size_t)sm * N + n) * F + i) * B + k] = in.T[o] > s.floor_nmf ? g.gT[(size_t)sm * N * FBp + o] : 0.f;
         }
     }
 }
@@ -343,7 +343,7 @@ __global__ void grad_v0_kernel(const Shape s, const StatePtrs* __restrict__ init
     const float* vin = init_tab[sm].V + (size_t)row * Jp;
     const float* src = gV + ((size_t)sm * N * B + row) * Jp;
     float* dst = gV0 + ((size_t)sm * N * B + row) * J;
-    for (int j = threadIdx.x; j < J; j += blockDim.x) dst[j] = vin[j] > kFloorNmf ? src[j] : 0.f;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) dst[j] = vin[j] > s.floor_nmf ? src[j] : 0.f;
 }
 
 // ---------------------------------------------------------------- state copies (checkpoints)
@@ -365,7 +365,7 @@ __global__ void grad_copy_kernel(const Shape s, const StatePtrs* __restrict__ sr
 }
 
 // ---------------------------------------------------------------- finalize with sigma record
-// As finalize_kernel (the pending normalisation applied to Y, W, log|det|, T) for every
+// As finalize_kernel (the pending normalisation applied to Y, W, log|det|, T, 1/lambda) for every
 // mixture of the batch; also records sigma_r = the applied scale.
 __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* __restrict__ sig)
 {
@@ -391,7 +391,13 @@ __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* _
         d.ldm[i] = 1.0;
         d.lde[i] = 0;
     }
-    if (s.row_l[r] == 0 && (int)threadIdx.x < B) d.T[(size_t)s.row_n[r] * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
+    if (s.row_l[r] == 0) {
+        const int n = s.row_n[r];
+        if ((int)threadIdx.x < B) d.T[(size_t)n * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
+        float* il = d.invlam + ((size_t)i * s.N + n) * Jp;        // 1/lambda with the normalised bases
+        const float fac = 1.0f / (sc * sc);
+        for (int j = threadIdx.x; j < Jp; j += blockDim.x) il[j] = scaled_invlam(il[j], fac);
+    }
     if (i == 0 && threadIdx.x == 0) sig[sm * M + r] = sc;
 }
 

@@ -120,6 +120,7 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     };
 
     // ---- forward ISS sweep (Eqs. 11-16), keeping z, d, q of every step
+    const double invJd = 1.0 / (double)J;
     float2 y[M][FPT];
 #pragma unroll
     for (int r = 0; r < M; ++r)
@@ -163,7 +164,7 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
                 dsv[r][p] = d;
             }
             const float qv = bout[VF - 1] / (float)J;
-            const float sr = qv > 0.f ? 1.f / sqrtf(qv) : 1.f;
+            const float sr = iss_normaliser(bout[VF - 1], invJd);      // as the forward sweep (FP64)
             z[r] = make_float2(1.f - sr, 0.f);
             zs[r][r] = z[r];
             dsv[r][r] = qv;
@@ -299,7 +300,7 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         const int n = t / B, k = t - n * B;
         const float T = Ti[t], T1 = T1i[t], g1 = gT1[t], dn = denT[t];
         float gTd = 0.f, gn = 0.f, gd = 0.f;
-        if (T1 > 1.0001f * kFloorNmf && T > 0.f && dn > 0.f) {
+        if (T1 > 1.0001f * s.floor_nmf && T > 0.f && dn > 0.f) {
             const float R = T1 / T, gR = g1 * T;
             gTd = g1 * R;
             gn = gR / (2.f * R * dn);

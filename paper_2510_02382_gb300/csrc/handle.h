@@ -44,7 +44,7 @@ struct TraceRange {
 };
 
 // kernels enqueued by one ctfmnmf_iterate of n_iter iterations on the two-kernel path
-long long iteration_kernels(int n_iter);
+long long iteration_kernels(int n_iter, bool scan);
 // finalize kernels (pending normalisation) launched at the end of every iterate call
 constexpr int kFinalizeKernels = 2;
 }  // namespace ctf

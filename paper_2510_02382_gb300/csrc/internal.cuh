@@ -9,10 +9,13 @@
 //   T      [N][FBp]    float32    bases, T[n][i][k] at n*FBp + i*B + k (the API shape [N][F][B]
 //                                 with each source block padded to 16 bytes)
 //   V      [N][B][Jp]  float32    activations (padding frames are 0)
-//   invlam [F][N][Jp]  float32    1/lambda_{n,i,j} for the current T, V (padding 0)
+//   invlam [F][N][Jp]  float32    1/lambda_{n,i,j} for the current V and the bases T' before
+//                                 the pending normalisation (padding 0): the bin phase
+//                                 multiplies it by mu_{(n,0)}^2 = 1/scale_{(n,0)}^2
 //   P      [F][N][Jp]  float32    delayed row power feeding the activation update
-//   mupart [F][M]      float32    per-bin row power sums feeding the normalisation
+//   mupart [F][M]      float64    per-bin row power sums feeding the normalisation
 //   scale  [M]         float32    pending normalisation 1/mu_r not yet applied to Y, W, T
+//                                 and 1/lambda
 //   ldm, lde [F]       f64, i32   running product of |det| factors (mantissa, exponent),
 //                                 folded into logdet at the end of every iterate call
 #pragma once
@@ -24,7 +27,7 @@
 
 namespace ctf {
 
-constexpr float kFloorNmf = 1e-12f;   // floor of T and V after each multiplicative update
+constexpr float kFloorNmf = 1e-12f;   // default floor of T and V after each multiplicative update
 constexpr float kFloorPsd = 1e-18f;   // floor of lambda where it is formed
 
 struct Shape {
@@ -34,6 +37,10 @@ struct Shape {
     int row_n[CTFMNMF_MAX_M];   // extended row r -> source n
     int row_l[CTFMNMF_MAX_M];   // extended row r -> tap l
     int row0[CTFMNMF_MAX_M];    // source n -> its tap-0 row
+    int det_reduce;             // 1: every reduction in a fixed order (ctfmnmf_options)
+    float floor_nmf;            // floor of T and V after each multiplicative update
+                                // (ctfmnmf_options.eps_floor, default kFloorNmf)
+    double invJ;                // 1/J in FP64 (the 1/J of Eq. 8 in the ISS normaliser)
 };
 
 struct State {
@@ -44,12 +51,13 @@ struct State {
     float* V;
     float* invlam;
     float* P;
-    float* mupart;
+    double* mupart;
     float* scale;
     double* ldm;        // [F] mantissa of the log-det product not yet folded into logdet
     int* lde;           // [F] its binary exponent
     unsigned* sync;     // grid barrier words: [0] abort, [1] arrivals, [2] generation
-    int* flag;          // [0]: non-finite input seen, [1]: device wait timed out
+    int* flag;          // [0]: non-finite input seen, [1]: device wait timed out,
+                        // [2]: NaN/Inf found after an iteration, [3]: a debug bounds check failed
     double* cost_part;  // [F] per-bin cost
     double* cost_out;   // [1]
     float2* staging;    // host-loaded STFT staging [M][F][J]
@@ -76,6 +84,8 @@ cudaError_t configure_frame_phase();
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st);
 cudaError_t launch_finalize(const Shape& s, const State& d, cudaStream_t st);
+// NaN/Inf scan of Y, T, V: sets flag[2] if any value is not finite (kernels.cu)
+cudaError_t launch_finite_scan(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t launch_cost(const Shape& s, const State& d, cudaStream_t st);
 cudaError_t launch_separate(const Shape& s, const State& d, float2* out, cudaStream_t st);
 cudaError_t launch_get_demixed(const Shape& s, const State& d, float2* out, cudaStream_t st);
@@ -164,6 +174,24 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The ISS normaliser of Eq. 16 for p = r: 1 - z_r = q^{-1/2}, q = (1/J) sum_j phi_r |y_r|^2,
+// formed and inverted in FP64 from the FP32 frame sum (invJ = 1/J in FP64); 1 for a row
+// without energy. FP64 on this GPU issues at about 1/64 of the FP32 rate whatever the active
+// lanes, so callers take the value off their critical path (it is needed only once the
+// sweep is over, see bin_body).
+__device__ __forceinline__ float iss_normaliser(float sum, double invJ)
+{
+    if (!(sum > 0.f)) return 1.0f;
+    return (float)rsqrt((double)sum * invJ);
+}
+
+// The pending normalisation of Eqs. 19-21 applied to a stored 1/lambda (formed from the bases
+// before it): 1/lambda'' = mu^2 / lambda' with mu = 1/s0, kept below the 1/floor of lambda.
+__device__ __forceinline__ float scaled_invlam(float w, float fac)
+{
+    return fminf(w * fac, 1.0f / kFloorPsd);
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -107,7 +107,7 @@ __global__ void init_nmf_kernel(const Shape s, const State d, const float* __res
             else if (use_default) v = default_factor(seed, 2 * e);
             else continue;
             bad |= !isfinite(v);
-            d.T[(size_t)n * s.FBp + (size_t)i * B + k] = fmaxf(v, kFloorNmf);
+            d.T[(size_t)n * s.FBp + (size_t)i * B + k] = fmaxf(v, s.floor_nmf);
         } else {
             const size_t f = e - nT;               // index into V [N][B][Jp]
             const int j = (int)(f % Jp);
@@ -119,7 +119,7 @@ __global__ void init_nmf_kernel(const Shape s, const State d, const float* __res
                 else if (use_default) v = default_factor(seed, 2 * src + 1);
                 else continue;
                 bad |= !isfinite(v);
-                v = fmaxf(v, kFloorNmf);
+                v = fmaxf(v, s.floor_nmf);
             }
             d.V[f] = v;
         }
@@ -165,9 +165,10 @@ cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st)
 }
 
 // ------------------------------------------------------------------ frame phase
-// Two-kernel path: one CTA (one group of 256 threads) per (8-frame tile, source) item; the
-// device code is frame_item() in phases.cuh. The CTA first forms the normalisation scale
-// from the per-bin row powers; CTA 0 stores it as the pending scale of the next bin phase.
+// Two-kernel path: block 0 forms the normalisation scale of this iteration from the per-bin
+// row powers (FP64, Eq. 19) and stores it as the pending scale of the next bin phase; every
+// other block (256 threads) takes one (8-frame tile, source) item, whose device code is
+// frame_item() in phases.cuh (the items need no scale: the next bin phase applies it).
 constexpr int kFrameThreads = 256;
 constexpr int kFrameSmemBytes = 48 * 1024;
 
@@ -178,15 +179,21 @@ __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape 
                                                                     const int FC)
 {
     extern __shared__ float4 fsm4[];
-    __shared__ float s_scale[CTFMNMF_MAX_M];
-    __shared__ float red_cta[(kFrameThreads / 32) * CTFMNMF_MAX_M];
+#ifdef CTFMNMF_DEBUG
+    if ((int)blockIdx.x > (s.Jp / kFrameTile) * s.N) {     // an item outside the shape
+        if (threadIdx.x == 0) atomicOr(d.flag + 3, 1);
+        return;
+    }
+#endif
+    if (blockIdx.x == 0) {
+        scales_fp64(s, d, normalize, reinterpret_cast<double*>(fsm4));
+        return;
+    }
     const Grp g{(int)threadIdx.x, kFrameThreads, 0};
-    const ScaleJob job{s_scale, red_cta, normalize};     // formed while the item's staging is in flight
     if constexpr (BB <= 16)
-        frame_item<BB, EXACT>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
+        frame_item<BB, EXACT>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
     else
-        frame_item_wide<BB, EXACT>(s, d, blockIdx.x, g, reinterpret_cast<float*>(fsm4), FC, s_scale, v_tap0, &job);
-    if (blockIdx.x == 0 && threadIdx.x < s.M) d.scale[threadIdx.x] = s_scale[threadIdx.x];
+        frame_item_wide<BB, EXACT>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
 }
 
 static int frame_fc(const Shape& s, int BB)
@@ -232,7 +239,7 @@ static void frame_launch(const Shape& s, const State& d, int v_tap0, int normali
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st)
 {
-    const int items = (s.Jp / kFrameTile) * s.N;
+    const int items = (s.Jp / kFrameTile) * s.N + 1;       // + block 0, the scale
     const int BB = frame_bb(s.B);
     const int FC = frame_fc(s, BB);
     if (FC < 4 || (FC * s.B) % 4 != 0 || s.Jp % kFrameTile != 0) return cudaErrorInvalidValue;
@@ -248,8 +255,8 @@ cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int n
 }
 
 // ------------------------------------------------------------------ finalize
-// Apply the pending normalisation (scale) to Y rows, W rows, log|det| and T, after the
-// last iteration of a call. One CTA per (bin, row).
+// Apply the pending normalisation (scale) to Y rows, W rows, log|det|, T and the stored
+// 1/lambda, after the last iteration of a call. One CTA per (bin, row).
 __global__ void finalize_kernel(const Shape s, const State d)
 {
     const int i = blockIdx.x, r = blockIdx.y;
@@ -272,10 +279,35 @@ __global__ void finalize_kernel(const Shape s, const State d)
         d.ldm[i] = 1.0;
         d.lde[i] = 0;
     }
-    if (s.row_l[r] == 0 && threadIdx.x < B) {
+    if (s.row_l[r] == 0) {
         const int n = s.row_n[r];
-        d.T[(size_t)n * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
+        if (threadIdx.x < B) d.T[(size_t)n * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
+        float* il = d.invlam + ((size_t)i * s.N + n) * Jp;
+        const float fac = 1.0f / (sc * sc);
+        for (int j = threadIdx.x; j < Jp; j += blockDim.x) il[j] = scaled_invlam(il[j], fac);
     }
+}
+
+// ------------------------------------------------------------------ NaN/Inf scan
+// Y [F][M][Jp] complex64, T [N][FBp] and V [N][B][Jp] float32: flag[2] is set if any value is
+// not finite (ctfmnmf_options.check_finite, and every iteration of a CTFMNMF_DEBUG build).
+__global__ void finite_scan_kernel(const Shape s, const State d)
+{
+    const size_t nY = (size_t)s.F * s.M * s.Jp * 2, nT = (size_t)s.N * s.FBp, nV = (size_t)s.N * s.B * s.Jp;
+    const float* Yf = reinterpret_cast<const float*>(d.Y);
+    bool bad = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nY + nT + nV;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const float v = e < nY ? Yf[e] : e < nY + nT ? d.T[e - nY] : d.V[e - nY - nT];
+        bad |= !isfinite(v);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(d.flag + 2, 1);
+}
+
+cudaError_t launch_finite_scan(const Shape& s, const State& d, cudaStream_t st)
+{
+    finite_scan_kernel<<<304, 256, 0, st>>>(s, d);
+    return cudaGetLastError();
 }
 
 __global__ void reset_scale_kernel(const Shape s, const State d)

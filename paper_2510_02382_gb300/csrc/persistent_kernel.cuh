@@ -2,8 +2,8 @@
 // launch. Each CTA holds G groups; group k of CTA b owns bins b*G + k, + G*gridDim, ...
 // Per iteration:
 //   bin phase (ISS sweep + basis MU of its bins, Sec. III) -> grid barrier ->
-//   every CTA forms mu (Eq. 19); frame items (activation MU + next PSD, Eqs. 18-21) ->
-//   grid barrier.
+//   frame items (activation MU + next PSD, Eq. 18), and the last CTA forms mu in FP64
+//   (Eq. 19) as the pending scale -> grid barrier (every CTA then reads the scale).
 // When every group owns at most one bin and the shared memory allows, the bin's rows and
 // W_i stay in shared memory across iterations ("resident"): Y is read from and written to
 // HBM once per call instead of once per iteration.
@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 persistent_kernel(const Shape s, const State d, const PersistArgs pa)
 {
     extern __shared__ float4 psm4[];
-    __shared__ float s_old[CTFMNMF_MAX_M], s_new[CTFMNMF_MAX_M];
-    __shared__ float red_cta[(kPersistThreads / 32) * CTFMNMF_MAX_M];
+    __shared__ float s_old[CTFMNMF_MAX_M];
+    __shared__ double red_cta[(kPersistThreads / 32) * CTFMNMF_MAX_M];
     // Shared memory: [group 0 work | ... | group G-1 work | group 0 rows | ... ]; the frame
     // phase uses the G work regions as one CTA-wide region.
     const int G = pa.groups, GT = pa.gt;
@@ -148,19 +148,18 @@ persistent_kernel(const Shape s, const State d, const PersistArgs pa)
         }
         alive = grid_sync(d, 2u * it + 1u, pa.timeout_ns, it == 0 && (int)blockIdx.x == pa.skip_cta);
         if (!alive) break;
-        // ---- normalisation scale and frame items
-        // the first item of the CTA also forms the scale, overlapping its staging copies
-        const ScaleJob job{s_new, red_cta, pa.normalize};
-        bool scaled = false;
+        // ---- frame items; the last CTA also forms the normalisation scale (FP64) into d.scale
         for (int item = blockIdx.x; item < items; item += gridDim.x) {
             // two frames per thread where the registers allow it (128 per thread here)
-            if constexpr (BB <= 10) frame_item<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0, scaled ? nullptr : &job);
-            else frame_item_wide<BB>(s, d, item, cta, psm, pa.fc, s_new, pa.v_tap0, scaled ? nullptr : &job);
-            scaled = true;
+            if constexpr (BB <= 10) frame_item<BB>(s, d, item, cta, psm, pa.fc, pa.v_tap0);
+            else frame_item_wide<BB>(s, d, item, cta, psm, pa.fc, pa.v_tap0);
         }
-        if (!scaled) compute_scales(s, d, pa.normalize, s_new, red_cta);
+        if (blockIdx.x == gridDim.x - 1) {
+            scales_fp64(s, d, pa.normalize, red_cta);
+            __syncthreads();
+        }
         alive = grid_sync(d, 2u * it + 2u, pa.timeout_ns, false);
-        if (threadIdx.x < CTFMNMF_MAX_M) s_old[threadIdx.x] = s_new[threadIdx.x];
+        if (threadIdx.x < CTFMNMF_MAX_M) s_old[threadIdx.x] = (int)threadIdx.x < M ? __ldcg(d.scale + threadIdx.x) : 1.f;
         __syncthreads();
     }
     if (!alive) return;
@@ -170,7 +169,6 @@ persistent_kernel(const Shape s, const State d, const PersistArgs pa)
         for (int e = g.tid; e < M * Jp; e += GT) __stcg(Yb + e, Yres[e]);
         for (int e = g.tid; e < M * M; e += GT) __stcg(d.W + (size_t)gid * M * M + e, Wres[e]);
     }
-    if (blockIdx.x == 0 && threadIdx.x < M) d.scale[threadIdx.x] = s_old[threadIdx.x];
 }
 
 // Per-M instantiation tables (persistent_m*.cu), compiled as separate translation units.

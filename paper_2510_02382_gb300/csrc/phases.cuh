@@ -52,7 +52,7 @@ __device__ __forceinline__ void reduce_scatter(float (&a)[V], int lane)
 // ---------------------------------------------------------------------------------------
 // Bin phase: shared memory of a group (floats), ragged sizes rounded so float4 views align
 struct BinSmem {
-    int ils, cw, sq, red, red2, tpre, total;   // offsets (floats)
+    int ils, cw, sq, red, red2, tpre, scr, total;   // offsets (floats)
 };
 
 __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
@@ -65,7 +65,8 @@ __host__ __device__ inline BinSmem bin_smem_layout(int M, int N, int Jp, int nt)
     b.red = b.sq + M * Jp;                       // [2][NW][32]   ISS partials
     b.red2 = b.red + 2 * NW * 32;                // [NW][N][2][32] basis-update partials
     b.tpre = b.red2 + NW * N * 2 * 32;           // [N * B] this bin's bases, prefetched
-    b.total = b.tpre + N * CTFMNMF_MAX_B;        // (row powers [NW][8] reuse red)
+    b.scr = b.tpre + N * CTFMNMF_MAX_B;          // [8] the sweep's normalisers 1 - z_r
+    b.total = b.scr + CTFMNMF_MAX_M;             // (row powers [NW][8] reuse red)
     b.total = (b.total + 3) & ~3;
     return b;
 }
@@ -195,11 +196,12 @@ __device__ __forceinline__ void ip_solve_warp(const float* Qs, float2* W, float*
 // One CTF-MNMF-ISS bin update (Sec. III) for bin i by group g.
 //   in:  y  = the bin's rows with the pending normalisation applied (frames g.tid + f*g.nt)
 //        wcol (threads g.tid < M) = column g.tid of W_i with the pending scale applied
-//        scale[r] = pending 1/mu_r (only used for T: T'' = T * scale_{(n,0)}^2)
+//        scale[r] = pending 1/mu_r (for T: T'' = T * scale_{(n,0)}^2, and for the stored
+//        1/lambda: times scale_{(n,0)}^{-2})
 //   out: the swept rows and W_i (Eqs. 11-16) stored to Ydst [M][Jp] / Wdst [M][M] (HBM when
 //        GLOBAL, else a shared-memory copy); T[i] by the basis MU (Eq. 17);
 //        P[i] (delayed power, or |y_{(n,0)}|^2 for the tap-0 activation update);
-//        mupart[i][r] = sum_j |y_r(j)|^2;
+//        mupart[i][r] = sum_j |y_r(j)|^2 (FP64);
 //        returns prod_r (1 - z_r), the factor of |det W_i| (Eq. 13).
 // IP = true replaces the ISS sweep by the IP update of Eqs. 9-10 (M <= 4): the weighted
 // covariances Q_r (Eq. 8) of the kept observation d.X, the sequential solves (ip_solve_warp),
@@ -222,6 +224,7 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
     float* red = gsm + L.red;
     float* red2 = gsm + L.red2;
     float* tpre = gsm + L.tpre;
+    float* s_scr = gsm + L.scr;
 
     // ---- prefetch this bin's bases (used at the end; the load overlaps the staging)
     for (int t = g.tid; t < N * B; t += g.nt) {
@@ -229,7 +232,9 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         tpre[t] = __ldcg(d.T + (size_t)n * s.FBp + (size_t)i * B + k);
     }
 
-    // ---- stage 1/lambda of this bin (cp.async, 16 bytes per copy; zero front pad)
+    // ---- stage 1/lambda of this bin (cp.async, 16 bytes per copy; zero front pad). The stored
+    //      1/lambda is formed from the bases before the pending normalisation: each thread
+    //      scales the entries it copied by mu_{(n,0)}^2 once its own copies have landed.
     {
         const float4* src = reinterpret_cast<const float4*>(d.invlam + (size_t)i * N * Jp);
         float4* dst = reinterpret_cast<float4*>(ils);
@@ -241,6 +246,17 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
                 else cp_async16(dst + e, src + (size_t)n * J4 + o - P4);
             }
         cp_async_wait();
+        for (int n = 0; n < N; ++n) {
+            const float s0 = scale[s.row0[n]];
+            const float fac = 1.0f / (s0 * s0);
+            for (int o = g.tid; o < LR4; o += g.nt) {
+                if (o < P4) continue;
+                float4 v = dst[n * LR4 + o];
+                v = make_float4(scaled_invlam(v.x, fac), scaled_invlam(v.y, fac), scaled_invlam(v.z, fac),
+                                scaled_invlam(v.w, fac));
+                dst[n * LR4 + o] = v;
+            }
+        }
     }
     grp_sync(g);
 
@@ -380,14 +396,12 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
                 z[p] = make_float2(tot[c] * inv, tot[c + 1] * inv);
             }
         }
-        // 1 - z_r = q^{-1/2}, q = (1/J) sum_j phi_r |y_r|^2: FP32 rsqrt and one Newton step
-        const float q = tot[r] * invJ;
-        float sc = 1.0f;
-        if (q > 0.f) {
-            const float r0 = rsqrtf(q);
-            sc = r0 * fmaf(-0.5f * q * r0, r0, 1.5f);
-        }
-        detf *= sc;
+        // 1 - z_r = q^{-1/2}, q = (1/J) sum_j phi_r |y_r|^2, is formed in FP64 at the end of the
+        // sweep from this frame sum (kept in shared memory until then). Row r (of Y and of W) is scaled only then: every later step is
+        // linear and homogeneous in it (its z_r is the ratio of a sum linear in y_r to one
+        // without it, and its update subtracts z_r times another row), so the deferred scale
+        // gives the same rows.
+        if (g.tid == 0) s_scr[r] = tot[r];
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const float2 yr = y[r][f];
@@ -397,7 +411,6 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
                 y[p][f].x -= z[p].x * yr.x - z[p].y * yr.y;
                 y[p][f].y -= z[p].x * yr.y + z[p].y * yr.x;
             }
-            y[r][f] = make_float2(yr.x * sc, yr.y * sc);
         }
         if (g.tid < M) {
             const float2 wr = wcol[r];
@@ -407,8 +420,24 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
                 wcol[p].x -= z[p].x * wr.x - z[p].y * wr.y;
                 wcol[p].y -= z[p].x * wr.y + z[p].y * wr.x;
             }
-            wcol[r] = make_float2(wr.x * sc, wr.y * sc);
         }
+    }
+    // the FP64 normalisers of all rows by warp 0, one row per lane (an FP64 instruction costs
+    // the same for one lane as for 32 on this GPU), published with one barrier
+    if (warp == 0) {
+        __syncwarp();
+        const float sc = iss_normaliser(lane < M ? s_scr[lane] : 0.f, s.invJ);
+        __syncwarp();
+        if (lane < M) s_scr[lane] = sc;
+    }
+    grp_sync(g);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        const float sc = s_scr[r];
+        detf *= sc;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) y[r][f] = make_float2(y[r][f].x * sc, y[r][f].y * sc);
+        if (g.tid < M) wcol[r] = make_float2(wcol[r].x * sc, wcol[r].y * sc);
     }
     }   // ISS
 
@@ -542,11 +571,11 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         float* Tp = d.T + (size_t)n * s.FBp + (size_t)i * B + k;
         const float tcur = tpre[t] * (s0 * s0);
         const float tn = (den > 0.f) ? tcur * sqrtf(num / den) : tcur;
-        __stcg(Tp, fmaxf(tn, kFloorNmf));
+        __stcg(Tp, fmaxf(tn, s.floor_nmf));
     }
-    if (g.tid < M) {
-        float t = 0.f;
-        for (int w = 0; w < NW; ++w) t += red[w * 8 + g.tid];
+    if (g.tid < M) {                                  // the bin's row power in FP64 (Eq. 19)
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += (double)red[w * 8 + g.tid];
         __stcg(d.mupart + (size_t)i * M + g.tid, t);
     }
     grp_sync(g);     // shared memory is reused by the next item of this group
@@ -646,16 +675,18 @@ __host__ __device__ inline int frame_chunk(int avail_floats, int B, int fixed)
     return ((avail_floats - fixed) / (B + kFrameTile)) & ~3;   // multiple of 4: Ps stays 16-byte aligned
 }
 
-// mu_r and the pending scale 1/mu_r from the per-bin row powers (Eq. 19), FP32 tree sums;
-// computed by the whole CTA into scale_out[M] (shared). Uses red_cta[8 * 32] as scratch.
-__device__ __forceinline__ void compute_scales(const Shape& s, const State& d, int normalize,
-                                               float* scale_out, float* red_cta)
+// mu_r^2 = (1/(F J)) sum_i mupart[i][r] (Eq. 19) summed over the bins in FP64, and the pending
+// scale 1/mu_r (1 without normalisation, or for a row without energy), by one whole block;
+// thread r < M stores it to d.scale[r]. Run once per iteration and mixture, by a block of
+// its own, so that its FP64 work (slow on this GPU) is off every other block's path.
+// red_cta: shared scratch of (blockDim.x / 32) * CTFMNMF_MAX_M doubles.
+__device__ __forceinline__ void scales_fp64(const Shape& s, const State& d, int normalize, double* red_cta)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int M = s.M, F = s.F;
-    float acc[CTFMNMF_MAX_M];
+    double acc[CTFMNMF_MAX_M];
 #pragma unroll
-    for (int r = 0; r < CTFMNMF_MAX_M; ++r) acc[r] = 0.f;
+    for (int r = 0; r < CTFMNMF_MAX_M; ++r) acc[r] = 0.0;
     for (int i = tid; i < F; i += blockDim.x) {
 #pragma unroll
         for (int r = 0; r < CTFMNMF_MAX_M; ++r)
@@ -664,22 +695,16 @@ __device__ __forceinline__ void compute_scales(const Shape& s, const State& d, i
 #pragma unroll
     for (int r = 0; r < CTFMNMF_MAX_M; ++r) {
         if (r >= M) break;
-        const float v = warp_sum(acc[r]);
+        const double v = warp_sum_d(acc[r]);
         if (lane == 0) red_cta[warp * CTFMNMF_MAX_M + r] = v;
     }
     __syncthreads();
     if (tid < M) {
-        float t = 0.f;
+        double t = 0.0;
         for (int w = 0; w < nw; ++w) t += red_cta[w * CTFMNMF_MAX_M + tid];
-        const float ms = t / ((float)F * (float)s.J);
-        float sc = 1.0f;
-        if (normalize && ms > 0.f) {
-            const float r0 = rsqrtf(ms);
-            sc = r0 * fmaf(-0.5f * ms * r0, r0, 1.5f);
-        }
-        scale_out[tid] = sc;
+        const double ms = t / ((double)F * (double)s.J);
+        d.scale[tid] = (normalize && ms > 0.0) ? (float)rsqrt(ms) : 1.0f;
     }
-    __syncthreads();
 }
 
 // Copy `count` contiguous floats of bases (16-byte aligned source; count rounded up to a
@@ -691,26 +716,17 @@ __device__ __forceinline__ void stage_bases(const float* src, float* dst, int co
         cp_async16(reinterpret_cast<float4*>(dst) + e, reinterpret_cast<const float4*>(src) + e);
 }
 
-// The normalisation scale (compute_scales) to be formed inside the first frame item of a
-// CTA, after that item's staging copies are issued, so that the two round trips overlap.
-// Only valid when the item's group is the whole CTA.
-struct ScaleJob {
-    float* out;        // shared [M]
-    float* red_cta;    // shared scratch [(blockDim/32) * CTFMNMF_MAX_M]
-    int normalize;
-};
-
-// One frame-phase item (Eq. 18, all-taps form by default, then Eqs. 19-21 for the PSD):
+// One frame-phase item (Eq. 18, all-taps form by default, then the next PSD):
 //   lambda'_{n,i,j} = sum_k T'[i][n][k] V[n][k][j],  T' = the bases of this iteration,
 //   num[k] = sum_i T'[i][n][k] P[i][n][j]/lambda'^2,  den[k] = sum_i T'[i][n][k] c_n(j)/lambda',
 //   V[n][k][j] <- max(V sqrt(num/den), floor),
-//   1/lambda for the next iteration with T'' = T' scale_{(n,0)}^2.
+//   1/lambda for the next iteration with T' and the new V; the normalisation of Eqs. 19-21
+//   (T'' = T' scale_{(n,0)}^2) is applied to it by the next bin phase.
 // Threads: tx = tid & 7 frame of the tile, ty = tid >> 3 bin slice (one frame per thread:
 // the variant for many bases, BB = 32).
 template <int BB, bool EXACT = false>
 __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, const int item, const Grp& g,
-                                           float* gsm, const int FC, const float* scale, const int v_tap0,
-                                           const ScaleJob* job = nullptr)
+                                           float* gsm, const int FC, const int v_tap0)
 {
     const int M = s.M, N = s.N, F = s.F, J = s.J, Jp = s.Jp;
     const int B = EXACT ? BB : s.B;     // EXACT: the bases count is the class width
@@ -744,7 +760,6 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
             cp_async16(reinterpret_cast<float4*>(Ps) + e,
                        reinterpret_cast<const float4*>(d.P + ((size_t)(c0 + ii) * N + n) * Jp + j0) + h);
         }
-        if (job && c0 == 0) compute_scales(s, d, job->normalize, job->out, job->red_cta);
         cp_async_wait();
         grp_sync(g);
         if (valid) {
@@ -798,16 +813,14 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
             float* Vp = d.V + ((size_t)n * B + k) * Jp + jj;
             const float vo = __ldcg(Vp);
             v = (den > 0.f) ? vo * sqrtf(num / den) : vo;
-            v = fmaxf(v, kFloorNmf);
+            v = fmaxf(v, s.floor_nmf);
             __stcg(Vp, v);
         }
         vnew[k * kFrameTile + x] = v;
     }
     grp_sync(g);
 
-    // ---- PSD of the next iteration with the normalised bases
-    const float s0 = scale[s.row0[n]];
-    const float t2 = s0 * s0;
+    // ---- PSD of the next iteration (bases before the normalisation)
 #pragma unroll
     for (int k = 0; k < BB; ++k) vk[k] = k < B ? vnew[k * kFrameTile + tx] : 0.f;
     for (int c0 = 0; c0 < F; c0 += FC) {
@@ -826,7 +839,7 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
                 if (k + 1 < BB && k + 1 < B) l1 = fmaf(Ti[k + 1], vk[k + 1], l1);
             }
             __stcg(d.invlam + ((size_t)(c0 + ii) * N + n) * Jp + j,
-                   valid ? recip(fmaxf((l0 + l1) * t2, kFloorPsd)) : 0.f);
+                   valid ? recip(fmaxf(l0 + l1, kFloorPsd)) : 0.f);
         }
         if (F > FC) grp_sync(g);
     }
@@ -839,8 +852,7 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
 // and j0 + 2tx + 1, ty = tid >> 2 is the bin slice.
 template <int BB, bool EXACT = false>
 __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
-                                           float* gsm, const int FC, const float* scale, const int v_tap0,
-                                           const ScaleJob* job = nullptr)
+                                           float* gsm, const int FC, const int v_tap0)
 {
     static_assert(BB % 2 == 0 && BB <= 16, "two-frame item needs an even BB <= 16");
     const int N = s.N, F = s.F, J = s.J, Jp = s.Jp;
@@ -881,7 +893,6 @@ __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const
             cp_async16(reinterpret_cast<float4*>(Ps) + e,
                        reinterpret_cast<const float4*>(d.P + ((size_t)(cb + ii) * N + n) * Jp + j0) + h);
         }
-        if (job && cb == 0) compute_scales(s, d, job->normalize, job->out, job->red_cta);
         cp_async_wait();
         grp_sync(g);
         for (int ii = ty; ii < nb; ii += NY) {
@@ -945,16 +956,14 @@ __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const
             float* Vp = d.V + ((size_t)n * B + k) * Jp + jj;
             const float vo = __ldcg(Vp);
             v = (den > 0.f) ? vo * sqrtf(num / den) : vo;
-            v = fmaxf(v, kFloorNmf);
+            v = fmaxf(v, s.floor_nmf);
             __stcg(Vp, v);
         }
         vnew[k * kFrameTile + x] = v;
     }
     grp_sync(g);
 
-    // ---- PSD of the next iteration with the normalised bases (two frames per thread)
-    const float s0 = scale[s.row0[n]];
-    const float t2 = s0 * s0;
+    // ---- PSD of the next iteration, bases before the normalisation (two frames per thread)
 #pragma unroll
     for (int k = 0; k < BB; ++k) {
         v0[k] = k < B ? vnew[k * kFrameTile + 2 * tx] : 0.f;
@@ -978,8 +987,8 @@ __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const
                 l1a = fmaf(ta, v1[k], l1a);
                 l1b = fmaf(tb, v1[k + 1], l1b);
             }
-            const float2 o = make_float2(va ? recip(fmaxf((l0a + l0b) * t2, kFloorPsd)) : 0.f,
-                                         vb ? recip(fmaxf((l1a + l1b) * t2, kFloorPsd)) : 0.f);
+            const float2 o = make_float2(va ? recip(fmaxf(l0a + l0b, kFloorPsd)) : 0.f,
+                                         vb ? recip(fmaxf(l1a + l1b, kFloorPsd)) : 0.f);
             __stcg(reinterpret_cast<float2*>(d.invlam + ((size_t)(cb + ii) * N + n) * Jp + ja), o);
         }
         if (F > FC) grp_sync(g);

@@ -82,6 +82,13 @@ def test_create_ex_checks_taps_and_options(lib):
     d5 = api.Dims(5, 2, 3, 4, 8, 32)
     assert lib.ctfmnmf_create_ex(ctypes.byref(d5), None, ctypes.byref(o), ctypes.byref(h)) == -7   # 8 needs M <= 4
     o.bin_fpt = 0
+    assert (o.eps_floor, o.deterministic_reduce, o.check_finite) == (0.0, 1, 0)
+    for field, bad in (("eps_floor", -1.0), ("eps_floor", float("nan")), ("eps_floor", float("inf")),
+                       ("deterministic_reduce", 2), ("check_finite", -1)):
+        good = getattr(o, field)
+        setattr(o, field, bad)
+        assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1, field
+        setattr(o, field, good)
     o.w_update = 5
     assert lib.ctfmnmf_create_ex(ctypes.byref(d), None, ctypes.byref(o), ctypes.byref(h)) == -1
     o.w_update = 1                                             # IP update
