@@ -81,9 +81,13 @@ typedef struct ctfmnmf_options {
                                   replaces (M <= 4, two-kernel path only, not in a batch;
                                   keeps a copy of X, 8*M*F*J more bytes)                */
     int bin_fpt;               /* frames per thread of the two-kernel bin phase: 1, 2, 4
-                                  or 8 (M <= 4) when it fits J; 0 (default): with path
-                                  AUTO timed among the candidates, else the fewest that
-                                  fit. EUNSUPPORTED if the value cannot run this shape  */
+                                  or 8 (M <= 4) frames strided by the block size when it
+                                  fits J; -8: eight consecutive frames per thread in the
+                                  kernel compiled for the default taps (M <= 4, taps as
+                                  ctfmnmf_create derives them, J <= 4096); 0 (default):
+                                  with path AUTO timed among the candidates, else the
+                                  fewest that fit. EUNSUPPORTED if the value cannot run
+                                  this shape                                              */
     float eps_floor;           /* floor of T and V after each multiplicative update and at
                                   set_init; 0 (default) = 1e-12. Must be >= 0 and finite  */
     int deterministic_reduce;  /* 1 (default): every reduction in a fixed order, so that a
@@ -259,7 +263,9 @@ typedef struct ctfmnmf_batch* ctfmnmf_batch_t;
  * creation (it times two iterations of each candidate plan on the handles' buffers, saving
  * and restoring their state, so creating a batch changes no handle; it allocates and frees
  * temporary device memory of about the size of the mixtures' state). Work runs on the
- * stream of handles[0]. Errors: EINVAL, ENOMEM, EUNSUPPORTED (no plan fits), ECUDA;
+ * stream of handles[0]. The candidate plans are numbered 2 * preference + merged (see
+ * ctfmnmf_batch_info); as a diagnostic, the environment variable CTFMNMF_BATCH_PLAN=k (k in
+ * 0..5) keeps only candidate k. Errors: EINVAL, ENOMEM, EUNSUPPORTED (no plan fits), ECUDA;
  * messages from ctfmnmf_last_error(NULL).
  */
 int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* out);
@@ -273,7 +279,9 @@ int ctfmnmf_batch_iterate(ctfmnmf_batch_t b, int n_iter);
 int ctfmnmf_batch_time(ctfmnmf_batch_t b, int n_iter, double* ms);
 
 /* Diagnostic: info[5] (host) = {mixtures, bin classes, frame classes, chosen candidate
- * plan (2 * eight-frames-preferred + merged-classes), kernels launched so far}. */
+ * plan (2 * preference + merged-classes; preference 0: the single-mixture shape, 1: eight
+ * strided frames per thread, 2: eight consecutive frames where the taps allow), kernels
+ * launched so far}. */
 int ctfmnmf_batch_info(ctfmnmf_batch_t b, int* info);
 
 /*

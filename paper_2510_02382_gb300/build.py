@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_NAME = "libctfmnmf.so"
 SOURCES = ["api.cpp", "batch_api.cpp", "kernels.cu", "bin_phase.cu", "batch.cu", "persistent.cu", "noalloc.cu", "grad.cu", "grad_api.cpp", "cluster_bin.cu"] + [f"{k}_m{m}.cu" for k in ("persistent", "bin_phase", "batch")
-                                                         for m in range(2, 9)] + [f"grad_bin_m{m}.cu" for m in range(2, 5)]
+                                                         for m in range(2, 9)] + [f"grad_bin_m{m}.cu" for m in range(2, 5)] \
+    + [f"bin_contig_m{m}.cu" for m in range(2, 5)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -132,8 +132,13 @@ static void choose_path(ctfmnmf* h)
     constexpr int kIters = 3;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // candidates: the persistent kernel, then the two-kernel path with each bin-phase shape
-    int fpts[4] = {0, 0, 0, 0}, nts[4] = {0, 0, 0, 0};
+    int fpts[5] = {0, 0, 0, 0, 0}, nts[5] = {0, 0, 0, 0, 0};
     int nc = ctf::bin_phase_candidates(h->s.M, h->s.J, fpts, nts);
+    if (ctf::contig_supported(h->s)) {                 // eight contiguous frames per thread
+        fpts[nc] = ctf::kBinContig;
+        nts[nc] = ctf::contig_threads(h->s);
+        ++nc;
+    }
     const int def_fpt = h->bin_fpt, def_nt = h->bin_nt;
     if (h->opt.bin_fpt != 0) {                          // a forced shape is the only candidate
         fpts[0] = def_fpt;
@@ -225,8 +230,9 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         if (o.w_update != CTFMNMF_W_ISS && o.w_update != CTFMNMF_W_IP)
             return fail(nullptr, CTFMNMF_EINVAL, "unknown w_update %d", o.w_update);
         if (o.reserved[0]) return fail(nullptr, CTFMNMF_EINVAL, "reserved options must be 0");
-        if (o.bin_fpt != 0 && o.bin_fpt != 1 && o.bin_fpt != 2 && o.bin_fpt != 4 && o.bin_fpt != 8)
-            return fail(nullptr, CTFMNMF_EINVAL, "bin_fpt must be 0, 1, 2, 4 or 8");
+        if (o.bin_fpt != 0 && o.bin_fpt != 1 && o.bin_fpt != 2 && o.bin_fpt != 4 && o.bin_fpt != 8 &&
+            o.bin_fpt != ctf::kBinContig)
+            return fail(nullptr, CTFMNMF_EINVAL, "bin_fpt must be 0, 1, 2, 4, 8 or -8");
         if (!(o.eps_floor >= 0.f) || !(o.eps_floor < 3.0e38f))
             return fail(nullptr, CTFMNMF_EINVAL, "eps_floor must be finite and >= 0");
         if ((o.deterministic_reduce != 0 && o.deterministic_reduce != 1) || (o.check_finite != 0 && o.check_finite != 1))
@@ -264,7 +270,12 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
     if (!one_block && J > ctf::cluster_max_frames(M))
         return fail(nullptr, CTFMNMF_EUNSUPPORTED, "J=%d frames is too long for M=%d (at most %d)", J, M,
                     ctf::cluster_max_frames(M));
-    if (o.bin_fpt != 0) {                          // a forced bin-phase shape must be a candidate
+    if (o.bin_fpt == ctf::kBinContig) {            // eight contiguous frames per thread, default taps
+        if (!ctf::contig_supported(s))
+            return fail(nullptr, CTFMNMF_EUNSUPPORTED, "bin_fpt=-8 needs M <= 4, the default taps and J <= 4096");
+        fpt = ctf::kBinContig;
+        nt = ctf::contig_threads(s);
+    } else if (o.bin_fpt != 0) {                   // a forced bin-phase shape must be a candidate
         int fpts[4], nts[4];
         const int nc = ctf::bin_phase_candidates(M, J, fpts, nts);
         int k = 0;

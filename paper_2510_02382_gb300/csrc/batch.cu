@@ -69,6 +69,12 @@ batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ w
 // ---------------------------------------------------------------- dispatch
 cudaError_t launch_batch_bin(const BatchClass& c, const MixDesc* mixes, int v_tap0, cudaStream_t st, bool configure)
 {
+    if (c.fpt == kBinContig) {
+        const Shape none_s = {};
+        const State none_d = {};
+        return contig_dispatch(c.M, c.N, c.kb, none_s, none_d, mixes, c.work, c.blocks, c.nt, c.smem, v_tap0, st,
+                               configure);
+    }
     switch (c.M) {
         case 2: return batch_bin_m2(c.fpt, c.kb, mixes, c.work, c.blocks, c.nt, c.smem, v_tap0, st, configure);
         case 3: return batch_bin_m3(c.fpt, c.kb, mixes, c.work, c.blocks, c.nt, c.smem, v_tap0, st, configure);

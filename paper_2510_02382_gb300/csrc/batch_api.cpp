@@ -10,6 +10,7 @@
 // restored after, so creating a batch leaves every handle unchanged.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -61,30 +62,43 @@ bool bin_shape(int M, int J, int pref, int* fpt, int* nt)
     return ctf::bin_phase_config(M, J, fpt, nt);
 }
 
+// pref 2: the contiguous-frame bin phase (ctf::kBinContig) for every mixture it supports
+// (M <= 4, default taps), preference 1 for the others.
 int make_plan(const std::vector<ctfmnmf*>& hs, int pref, bool merge, Plan* out)
 {
-    // key -> list of (mixture, F) ; key = (M, fpt, nt) with nt = 0 when merged
+    // key -> list of (mixture, F) ; key = (M, fpt, nt with 0 when merged, bases class, or
+    // 1000 + 16 N + bases groups for the contiguous-frame classes, compiled per N and groups)
     std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
     std::vector<int> mix_nt(hs.size());
     for (size_t b = 0; b < hs.size(); ++b) {
+        const Shape& s = hs[b]->s;
         int fpt = 0, nt = 0;
-        if (!bin_shape(hs[b]->s.M, hs[b]->s.J, pref, &fpt, &nt)) return CTFMNMF_EUNSUPPORTED;
+        if (pref == 2 && ctf::contig_supported(s)) {
+            fpt = ctf::kBinContig;
+            nt = ctf::contig_threads(s);
+        } else if (!bin_shape(s.M, s.J, pref == 2 ? 1 : pref, &fpt, &nt)) {
+            return CTFMNMF_EUNSUPPORTED;
+        }
         mix_nt[b] = nt;
-        groups[std::make_tuple(hs[b]->s.M, fpt, merge ? 0 : nt, ctf::bases_class(hs[b]->s.B))].push_back((int)b);
+        const int sub = fpt == ctf::kBinContig ? 1000 + 16 * s.N + ctf::contig_groups(s.B) : ctf::bases_class(s.B);
+        groups[std::make_tuple(s.M, fpt, merge ? 0 : nt, sub)].push_back((int)b);
     }
     for (auto& kv : groups) {
         BatchClass c;
         memset(&c, 0, sizeof(c));
         c.M = std::get<0>(kv.first);
         c.fpt = std::get<1>(kv.first);
-        c.kb = std::get<3>(kv.first);
+        const bool contig = c.fpt == ctf::kBinContig;
+        c.kb = contig ? (std::get<3>(kv.first) - 1000) % 16 : std::get<3>(kv.first);
+        c.N = contig ? (std::get<3>(kv.first) - 1000) / 16 : 0;
         int nt = 0;
         size_t smem = 0;
         std::vector<int2> work;
         for (int b : kv.second) nt = std::max(nt, mix_nt[b]);
         for (int b : kv.second) {
             const Shape& s = hs[b]->s;
-            smem = std::max(smem, sizeof(float) * (size_t)ctf::bin_smem_floats(s, nt));
+            smem = std::max(smem, contig ? ctf::contig_smem_bytes(s, nt)
+                                         : sizeof(float) * (size_t)ctf::bin_smem_floats(s, nt));
             for (int i = 0; i < s.F; ++i) work.push_back(make_int2(b, i));
         }
         c.nt = nt;
@@ -134,7 +148,7 @@ struct ctfmnmf_batch {
     std::vector<ctfmnmf*> hs;
     MixDesc* dmix;              // device [count]
     Plan plan;
-    int policy;                 // chosen candidate: 2 * pref + merge
+    int policy;                 // chosen candidate: 2 * pref + merge (pref 2: contiguous frames)
     int v_tap0, normalize;
     cudaStream_t capture;
     cudaGraphExec_t graph;
@@ -309,7 +323,13 @@ int ctfmnmf_batch_create(int count, const ctfmnmf_t* handles, ctfmnmf_batch_t* o
     Saved sv;
     if (rc == CTFMNMF_OK && !save_state(b->hs, &sv, st)) rc = fail_b(CTFMNMF_ENOMEM, "no memory to save state for tuning");
     float best = 1e30f;
-    for (int cand = 0; cand < 4 && rc == CTFMNMF_OK; ++cand) {
+    // diagnostic: CTFMNMF_BATCH_PLAN=k in the environment keeps only candidate k (0..5)
+    int only = -1;
+    if (const char* env = getenv("CTFMNMF_BATCH_PLAN")) {
+        if (env[0] >= '0' && env[0] <= '5' && env[1] == 0) only = env[0] - '0';
+    }
+    for (int cand = 0; cand < 6 && rc == CTFMNMF_OK; ++cand) {
+        if (only >= 0 && cand != only) continue;
         Plan p;
         const int prc = make_plan(b->hs, cand / 2, (cand & 1) != 0, &p);
         if (prc != CTFMNMF_OK || configure_plan(p, b->dmix) != cudaSuccess) {

@@ -2,9 +2,43 @@
 // handles created with the IP update, the IP sweep of Eqs. 9-10) and the basis update of
 // Sec. III for its bin (device code in phases.cuh, kernels in bin_phase_kernels.cuh). This
 // file holds the configuration and the dispatch over M.
-#include "phases.cuh"
+#include "bin_contig.cuh"
 
 namespace ctf {
+
+// contiguous-frame instantiations in bin_contig_m<M>.cu
+cudaError_t contig_launch_m2(int N, int GB, const Shape& s, const State& d, const MixDesc* mixes, const int2* work,
+                             int blocks, int nt, size_t smem, int v_tap0, cudaStream_t st, bool cfg);
+cudaError_t contig_launch_m3(int N, int GB, const Shape& s, const State& d, const MixDesc* mixes, const int2* work,
+                             int blocks, int nt, size_t smem, int v_tap0, cudaStream_t st, bool cfg);
+cudaError_t contig_launch_m4(int N, int GB, const Shape& s, const State& d, const MixDesc* mixes, const int2* work,
+                             int blocks, int nt, size_t smem, int v_tap0, cudaStream_t st, bool cfg);
+
+bool contig_supported(const Shape& s)
+{
+    if (s.M < 2 || s.M > 4 || s.N < 1 || s.N > s.M) return false;
+    for (int n = 0; n < s.N; ++n)
+        if (s.Ln[n] != s.M / s.N + (n < s.M % s.N ? 1 : 0)) return false;
+    return s.Jp % 8 == 0 && s.Jp <= kContigFpt * kContigMaxThreads;
+}
+
+int contig_threads(const Shape& s) { return (s.Jp / kContigFpt + 31) / 32 * 32; }
+
+size_t contig_smem_bytes(const Shape& s, int nt)
+{
+    return sizeof(float) * (size_t)contig_smem_layout(s.M, s.N, s.B, s.Jp, nt).total;
+}
+
+cudaError_t contig_dispatch(int M, int N, int GB, const Shape& s, const State& d, const MixDesc* mixes,
+                            const int2* work, int blocks, int nt, size_t smem, int v_tap0, cudaStream_t st, bool cfg)
+{
+    switch (M) {
+        case 2: return contig_launch_m2(N, GB, s, d, mixes, work, blocks, nt, smem, v_tap0, st, cfg);
+        case 3: return contig_launch_m3(N, GB, s, d, mixes, work, blocks, nt, smem, v_tap0, st, cfg);
+        case 4: return contig_launch_m4(N, GB, s, d, mixes, work, blocks, nt, smem, v_tap0, st, cfg);
+    }
+    return cudaErrorInvalidValue;
+}
 
 // instantiations in bin_phase_m<M>.cu
 cudaError_t bin_phase_m2(const Shape& s, const State& d, int v_tap0, int fpt, int nt, cudaStream_t st, bool cfg);
@@ -70,6 +104,11 @@ int bases_class(int B) { return B <= 4 ? 4 : B <= 8 ? 8 : B <= 10 ? 10 : 16; }
 static cudaError_t dispatch(const Shape& s, const State& d, int v_tap0, cudaStream_t st, bool cfg, int fpt = 0,
                             int nt = 0)
 {
+    if (fpt == kBinContig) {
+        if (!contig_supported(s) || nt != contig_threads(s)) return cudaErrorInvalidValue;
+        return contig_dispatch(s.M, s.N, contig_groups(s.B), s, d, nullptr, nullptr, s.F, nt, contig_smem_bytes(s, nt),
+                               v_tap0, st, cfg);
+    }
     if (fpt == 0 && !bin_phase_config(s.M, s.J, &fpt, &nt)) return cudaErrorInvalidValue;
     switch (s.M) {
         case 2: return bin_phase_m2(s, d, v_tap0, fpt, nt, st, cfg);

@@ -116,6 +116,8 @@ struct MixDesc {
 };
 struct BatchClass {
     int M, fpt, nt, blocks;
+    int N;             // contiguous-frame class (fpt == kBinContig): sources of every mixture;
+                       // its bases-group count is kept in kb
     int kb;            // bases per basis-MU pass (4, 8, 10, 16), covering every B of the class
     size_t smem;
     int2* work;        // device [blocks]
@@ -140,6 +142,19 @@ cudaError_t launch_cluster_bin_phase(const Shape& s, const State& d, int v_tap0,
                                      cudaStream_t st);
 // Frames of one bin a cluster of 8 blocks can hold (host rule, before any device query).
 inline int cluster_max_frames(int M) { return 8 * 512 * (M == 2 ? 8 : 4); }
+
+// Contiguous-frame bin phase (bin_contig.cuh; bin_fpt code kBinContig): 8 consecutive frames
+// per thread, compile-time default taps, M <= 4, J <= 4096.
+constexpr int kBinContig = -8;
+// Groups of 4 bases it is compiled for: 1 (B <= 4), 3 (B <= 12), 4 (B <= 16), 8 (B <= 32).
+__host__ __device__ constexpr int contig_groups(int B) { return B <= 4 ? 1 : B <= 12 ? 3 : B <= 16 ? 4 : 8; }
+bool contig_supported(const Shape& s);
+int contig_threads(const Shape& s);
+size_t contig_smem_bytes(const Shape& s, int nt);
+// M, N and bases groups GB of the launch; mixes == nullptr: the two-kernel kernel over s, d (s.F blocks), else the
+// batched kernel over `blocks` work items; cfg: raise the kernel's shared-memory limit only.
+cudaError_t contig_dispatch(int M, int N, int GB, const Shape& s, const State& d, const MixDesc* mixes,
+                            const int2* work, int blocks, int nt, size_t smem, int v_tap0, cudaStream_t st, bool cfg);
 
 // Set the message that ctfmnmf_last_error(NULL) returns on this thread.
 void set_thread_error(const char* msg);

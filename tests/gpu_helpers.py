@@ -17,9 +17,9 @@ def make_solver(mix, path="auto", **kw):
         raise
 
 
-def run_gpu(mix, n_iter, v_mode="all_taps", normalize=True, use_graph=True, set_init=True, path="auto"):
+def run_gpu(mix, n_iter, v_mode="all_taps", normalize=True, use_graph=True, set_init=True, path="auto", **kw):
     import torch
-    s = make_solver(mix, path=path, v_update=v_mode, normalize=normalize, use_graph=use_graph)
+    s = make_solver(mix, path=path, v_update=v_mode, normalize=normalize, use_graph=use_graph, **kw)
     X = torch.from_numpy(mix.X).cuda()
     s.load_stft(X)
     if set_init:

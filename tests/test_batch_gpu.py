@@ -186,3 +186,28 @@ def test_batched_workload_50_iterations_cost_on_sampled_mixtures():
     batch.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("plan", range(6))
+def test_every_batch_plan_matches_oracle(plan, monkeypatch):
+    """Each candidate plan of the batch autotuner (CTFMNMF_BATCH_PLAN keeps one): single-mixture
+    shapes, eight strided frames, eight consecutive frames where the taps allow (with the
+    strided kernel for the rest), each merged or not; ragged mixtures against the oracle."""
+    from paper_2510_02382_gb300.api import Batch
+    monkeypatch.setenv("CTFMNMF_BATCH_PLAN", str(plan))
+    mixes = [synth.random_case(800 + k, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+             for k, (M, N, Ln, F, J, B) in enumerate(RAGGED)]
+    solvers = _loaded(mixes)
+    batch = Batch(solvers)
+    assert batch.info()["plan"] == plan
+    batch.iterate(2)
+    for s, mix in zip(solvers, mixes):
+        r = run_oracle(mix, 2)
+        y = s.get_demixed().cpu().numpy()
+        assert rel_fro(y, r["y"]) < 1e-4 and per_bin_rel(y, r["y"]) < 1e-3, mix.spec
+        sp = mix.spec
+        ok, err = cost_close(s.cost(), r["cost"], 1e-5, sp.F, sp.J, sp.M)
+        assert ok, (sp, err)
+    batch.close()
+    for s in solvers:
+        s.close()

@@ -368,7 +368,44 @@ def test_table1_shapes_full_size_1_iteration(name):
     assert ok, err
 
 
-@pytest.mark.parametrize("fpt", [1, 2, 4, 8])
+# every default tap layout the contiguous-frame kernel is compiled for, ragged J, up to J = 4096
+CONTIG_SHAPES = [
+    # (M, N, F, J, B)
+    (2, 1, 5, 37, 3), (2, 2, 4, 1000, 10), (3, 1, 4, 301, 4), (3, 2, 6, 1001, 10), (3, 3, 3, 95, 16),
+    (4, 1, 3, 257, 2), (4, 2, 4, 2049, 5), (4, 3, 5, 4096, 16), (4, 4, 3, 64, 32), (3, 2, 3, 9, 1),
+]
+
+
+@pytest.mark.parametrize("shape", CONTIG_SHAPES, ids=lambda s: f"M{s[0]}N{s[1]}J{s[3]}B{s[4]}")
+def test_contiguous_frame_bin_phase_matches_oracle(shape):
+    """bin_fpt = -8: eight consecutive frames per thread, the taps compiled in; one iteration
+    against the oracle per bin (rows, W, T, V, log|det W|, images), three iterations' cost."""
+    M, N, F, J, B = shape
+    Ln = tuple(M // N + (1 if n < M % N else 0) for n in range(N))
+    mix = synth.random_case(6000 + 10 * M + N + J, M=M, N=N, F=F, J=J, B=B, Ln=Ln)
+    g = run_gpu(mix, 1, path="two_kernel", bin_fpt=-8)
+    r = run_oracle(mix, 1)
+    _check_state(g, r, mix)
+    g3, r3 = run_gpu(mix, 3, path="two_kernel", bin_fpt=-8), run_oracle(mix, 3)
+    ok, err = cost_close(g3["cost"], r3["cost"], 1e-5, F, J, M)
+    assert ok, err
+    for v_mode, norm in [("tap0", True), ("all_taps", False)]:
+        g = run_gpu(mix, 2, v_mode=v_mode, normalize=norm, path="two_kernel", bin_fpt=-8)
+        r = run_oracle(mix, 2, v_mode=v_mode, normalize=norm)
+        assert rel_fro(g["y"], r["y"]) < 1e-4, (v_mode, norm)
+
+
+def test_contiguous_frame_shape_needs_default_taps():
+    from paper_2510_02382_gb300.api import CTFMNMF, CtfMnmfError
+    with pytest.raises(CtfMnmfError) as e:
+        CTFMNMF(4, 2, 3, 3, 4, 100, Ln=(3, 1), path="two_kernel", bin_fpt=-8)      # not the default (2, 2)
+    assert e.value.name == "EUNSUPPORTED"
+    with pytest.raises(CtfMnmfError) as e:
+        CTFMNMF(5, 2, 3, 3, 4, 100, path="two_kernel", bin_fpt=-8)                 # M > 4
+    assert e.value.name == "EUNSUPPORTED"
+
+
+@pytest.mark.parametrize("fpt", [1, 2, 4, 8, -8])
 def test_every_bin_phase_shape_matches_oracle(fpt):
     """ctfmnmf_options.bin_fpt forces each two-kernel bin-phase shape AUTO chooses among;
     each must give the oracle's result (they differ only in how frames map to threads)."""
