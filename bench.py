@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--iters", type=int, default=None, help="iterations per step (default: workload's)")
     p.add_argument("--batched-steps", type=int, default=3,
                    help="timed steps of the 64-mixture batched workload (0 skips it)")
+    p.add_argument("--batched-mixtures", type=int, default=64,
+                   help="mixtures of the batched workload (seeds 0..n-1; fewer for small profiling captures)")
     p.add_argument("--fwdbwd-steps", type=int, default=3,
                    help="timed steps of the 16-mixture forward + backward workload (0 skips it)")
     p.add_argument("--longj-steps", type=int, default=3,
@@ -244,7 +246,7 @@ def batched_leg(args, peak):
     import torch
     from paper_2510_02382_gb300 import synth
     from paper_2510_02382_gb300.api import CTFMNMF, Batch
-    specs = synth.batched_specs()
+    specs = synth.batched_specs(count=args.batched_mixtures)
     solvers, bytes_it, binframes = [], 0, 0
     for sp in specs:
         mix = synth.make_mixture(sp)
@@ -264,8 +266,8 @@ def batched_leg(args, peak):
         sv.close()
     t = statistics.median(ms) / 1000.0
     achieved = bytes_it * iters / t / 1e9
-    return {"workload": "64 ragged mixtures: J ~ U[300, 3000], N in {2,3}, M = N+1, L in {2,4,8}, F=513, B=10, "
-                        "50 iterations per step, seeds 0..63",
+    return {"workload": f"{len(specs)} ragged mixtures: J ~ U[300, 3000], N in {{2,3}}, M = N+1, L in {{2,4,8}}, F=513, "
+                        f"B=10, 50 iterations per step, seeds 0..{len(specs) - 1}",
             "batch_iterations_per_s": iters / t, "bin_frames_per_s": binframes * iters / t,
             "ms_per_step": 1000.0 * t, "steps": len(ms),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
