@@ -61,9 +61,9 @@ batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ w
     const int fixed = frame_smem_fixed<BB>(kBatchFrameThreads);
     const int FC = frame_chunk(kBatchFrameSmemBytes / 4, s.B, fixed);
     if constexpr (BB <= 16)
-        frame_item<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
+        frame_item<BB, EXACT, true>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
     else
-        frame_item_wide<BB, EXACT>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
+        frame_item_wide<BB, EXACT, true>(s, d, w.y, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
 }
 
 // ---------------------------------------------------------------- dispatch

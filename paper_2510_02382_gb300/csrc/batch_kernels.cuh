@@ -40,7 +40,7 @@ batch_bin_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ wor
     if (threadIdx.x < CTFMNMF_MAX_M) s_scale[threadIdx.x] = (int)threadIdx.x < M ? d.scale[threadIdx.x] : 1.f;
     __syncthreads();
     apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
-    const float detf = bin_body<M, FPT, true, KB>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
+    const float detf = bin_body<M, FPT, true, KB, false, false, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
     if (g.tid == 0) {
         double f = (double)detf;
 #pragma unroll

@@ -30,7 +30,7 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
     if (threadIdx.x < CTFMNMF_MAX_M) s_scale[threadIdx.x] = (int)threadIdx.x < M ? d.scale[threadIdx.x] : 1.f;
     __syncthreads();
     apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
-    const float detf = bin_body<M, FPT, true, KB, false, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
+    const float detf = bin_body<M, FPT, true, KB, false, true, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
     if (g.tid == 0) {
         double f = (double)detf;
 #pragma unroll
@@ -57,7 +57,7 @@ ip_bin_kernel(const Shape s, const State d, const int v_tap0)
     if (threadIdx.x < CTFMNMF_MAX_M) s_scale[threadIdx.x] = (int)threadIdx.x < M ? d.scale[threadIdx.x] : 1.f;
     __syncthreads();
     apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
-    const float detf = bin_body<M, FPT, true, 16, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
+    const float detf = bin_body<M, FPT, true, 16, true, false, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
     if (g.tid == 0) {
         double f = (double)detf;
 #pragma unroll

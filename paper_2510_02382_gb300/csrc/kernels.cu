@@ -191,9 +191,9 @@ __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape 
     }
     const Grp g{(int)threadIdx.x, kFrameThreads, 0};
     if constexpr (BB <= 16)
-        frame_item<BB, EXACT>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
+        frame_item<BB, EXACT, true>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
     else
-        frame_item_wide<BB, EXACT>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
+        frame_item_wide<BB, EXACT, true>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
 }
 
 static int frame_fc(const Shape& s, int BB)

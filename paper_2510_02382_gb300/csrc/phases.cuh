@@ -207,7 +207,7 @@ __device__ __forceinline__ void ip_solve_warp(const float* Qs, float2* W, float*
 // covariances Q_r (Eq. 8) of the kept observation d.X, the sequential solves (ip_solve_warp),
 // then y = W x; the return value is then |det W_new| / |det W_old|.
 // VPRE = true loads the first V column of the basis update ahead of the barrier before it.
-template <int M, int FPT, bool GLOBAL, int KB = 16, bool IP = false, bool VPRE = false>
+template <int M, int FPT, bool GLOBAL, int KB = 16, bool IP = false, bool VPRE = false, bool ONE = false>
 __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const int i, const Grp& g,
                                           float* gsm, float2 (&y)[M][FPT], float2 (&wcol)[M],
                                           float2* Ydst, float2* Wdst, const float* scale, const int v_tap0)
@@ -578,7 +578,7 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         for (int w = 0; w < NW; ++w) t += (double)red[w * 8 + g.tid];
         __stcg(d.mupart + (size_t)i * M + g.tid, t);
     }
-    grp_sync(g);     // shared memory is reused by the next item of this group
+    if constexpr (!ONE) grp_sync(g);     // shared memory is reused by the next item of this group
     return detf;
 }
 
@@ -724,7 +724,7 @@ __device__ __forceinline__ void stage_bases(const float* src, float* dst, int co
 //   (T'' = T' scale_{(n,0)}^2) is applied to it by the next bin phase.
 // Threads: tx = tid & 7 frame of the tile, ty = tid >> 3 bin slice (one frame per thread:
 // the variant for many bases, BB = 32).
-template <int BB, bool EXACT = false>
+template <int BB, bool EXACT = false, bool ONE = false>
 __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, const int item, const Grp& g,
                                            float* gsm, const int FC, const int v_tap0)
 {
@@ -843,14 +843,14 @@ __device__ __forceinline__ void frame_item_wide(const Shape& s, const State& d, 
         }
         if (F > FC) grp_sync(g);
     }
-    grp_sync(g);     // shared memory is reused by the next item of this group
+    if constexpr (!ONE) grp_sync(g);     // shared memory is reused by the next item of this group
 }
 
 // The same item with two frames per thread (BB <= 16): each row of bases read from shared
 // memory feeds the two frames' PSD and both sums, and the reduction over the 8 bin slices
 // of a warp is a three-level reduce-scatter. Threads: tx = tid & 3 owns frames j0 + 2tx
 // and j0 + 2tx + 1, ty = tid >> 2 is the bin slice.
-template <int BB, bool EXACT = false>
+template <int BB, bool EXACT = false, bool ONE = false>
 __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const int item, const Grp& g,
                                            float* gsm, const int FC, const int v_tap0)
 {
@@ -993,7 +993,7 @@ __device__ __forceinline__ void frame_item(const Shape& s, const State& d, const
         }
         if (F > FC) grp_sync(g);
     }
-    grp_sync(g);     // shared memory is reused by the next item of this group
+    if constexpr (!ONE) grp_sync(g);     // shared memory is reused by the next item of this group
 }
 
 }  // namespace ctf
