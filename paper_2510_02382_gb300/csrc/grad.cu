@@ -366,39 +366,52 @@ __global__ void grad_copy_kernel(const Shape s, const StatePtrs* __restrict__ sr
 
 // ---------------------------------------------------------------- finalize with sigma record
 // As finalize_kernel (the pending normalisation applied to Y, W, log|det|, T, 1/lambda) for every
-// mixture of the batch; also records sigma_r = the applied scale.
+// mixture of the batch; also records sigma_r = the applied scale. One block per (bin, mixture)
+// covering all of its rows with 16-byte accesses (two complex values, four 1/lambda).
 __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* __restrict__ sig)
 {
-    const int i = blockIdx.x, r = blockIdx.y, sm = blockIdx.z;
+    const int i = blockIdx.x, sm = blockIdx.y;
     const Shape& s = mixes[sm].s;
     const State& d = mixes[sm].d;
-    const int M = s.M, B = s.B, Jp = s.Jp;
-    if (i >= s.F || r >= M) return;
-    const float sc = d.scale[r];
-    float2* row = d.Y + ((size_t)i * M + r) * Jp;
-    for (int j = threadIdx.x; j < Jp; j += blockDim.x) {
-        const float2 v = row[j];
-        row[j] = make_float2(v.x * sc, v.y * sc);
+    const int M = s.M, N = s.N, B = s.B, Jp = s.Jp;
+    if (i >= s.F) return;
+    __shared__ float sc[CTFMNMF_MAX_M];
+    if ((int)threadIdx.x < M) sc[threadIdx.x] = d.scale[threadIdx.x];
+    __syncthreads();
+    const int R4 = Jp >> 1;                              // float4 per row of Y
+    float4* Yb = reinterpret_cast<float4*>(d.Y + (size_t)i * M * Jp);
+    for (int e = threadIdx.x; e < M * R4; e += blockDim.x) {
+        const float c = sc[e / R4];
+        const float4 v = Yb[e];
+        Yb[e] = make_float4(v.x * c, v.y * c, v.z * c, v.w * c);
     }
-    if ((int)threadIdx.x < M) {
-        float2* w = d.W + ((size_t)i * M + r) * M + threadIdx.x;
-        *w = make_float2(w->x * sc, w->y * sc);
+    if ((int)threadIdx.x < M * M) {
+        float2* w = d.W + (size_t)i * M * M + threadIdx.x;
+        const float c = sc[threadIdx.x / M];
+        *w = make_float2(w->x * c, w->y * c);
     }
-    if (r == 0 && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         double f = d.ldm[i];
-        for (int p = 0; p < M; ++p) f *= (double)d.scale[p];
+        for (int p = 0; p < M; ++p) f *= (double)sc[p];
         d.logdet[i] += log(f) + (double)d.lde[i] * 0.69314718055994530942;
         d.ldm[i] = 1.0;
         d.lde[i] = 0;
     }
-    if (s.row_l[r] == 0) {
-        const int n = s.row_n[r];
-        if ((int)threadIdx.x < B) d.T[(size_t)n * s.FBp + (size_t)i * B + threadIdx.x] *= sc * sc;
-        float* il = d.invlam + ((size_t)i * s.N + n) * Jp;        // 1/lambda with the normalised bases
-        const float fac = 1.0f / (sc * sc);
-        for (int j = threadIdx.x; j < Jp; j += blockDim.x) il[j] = scaled_invlam(il[j], fac);
+    for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
+        const int n = t / B, k = t - n * B;
+        const float c = sc[s.row0[n]];
+        d.T[(size_t)n * s.FBp + (size_t)i * B + k] *= c * c;
     }
-    if (i == 0 && threadIdx.x == 0) sig[sm * M + r] = sc;
+    const int L4 = Jp >> 2;                              // float4 per row of 1/lambda
+    float4* il = reinterpret_cast<float4*>(d.invlam + (size_t)i * N * Jp);
+    for (int e = threadIdx.x; e < N * L4; e += blockDim.x) {
+        const float c = sc[s.row0[e / L4]];
+        const float fac = 1.0f / (c * c);
+        const float4 v = il[e];
+        il[e] = make_float4(scaled_invlam(v.x, fac), scaled_invlam(v.y, fac), scaled_invlam(v.z, fac),
+                            scaled_invlam(v.w, fac));
+    }
+    if (i == 0 && (int)threadIdx.x < M) sig[sm * M + threadIdx.x] = sc[threadIdx.x];
 }
 
 __global__ void grad_reset_scale_kernel(const MixDesc* __restrict__ mixes)
@@ -524,7 +537,7 @@ cudaError_t grad_launch_copy(const Shape& s, int S, const StatePtrs* src, const 
 
 cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, float* sig, cudaStream_t st)
 {
-    grad_finalize_kernel<<<dim3(s.F, s.M, S), 256, 0, st>>>(mixes, sig);
+    grad_finalize_kernel<<<dim3(s.F, S), 256, 0, st>>>(mixes, sig);
     grad_reset_scale_kernel<<<S, 32, 0, st>>>(mixes);
     return cudaGetLastError();
 }
