@@ -52,6 +52,8 @@ def parse():
                    help="mixtures of the batched workload (seeds 0..n-1; fewer for small profiling captures)")
     p.add_argument("--fwdbwd-steps", type=int, default=3,
                    help="timed steps of the 16-mixture forward + backward workload (0 skips it)")
+    p.add_argument("--fwdbwd-ckpt", type=int, default=0,
+                   help="checkpoint segment length of the forward + backward workload (0: all iterations)")
     p.add_argument("--longj-steps", type=int, default=3,
                    help="timed steps of the long-J workload (F=513, J=16000; 0 skips it)")
     p.add_argument("--path", default="auto", choices=["auto", "persistent", "two_kernel"],
@@ -277,7 +279,8 @@ def batched_leg(args, peak):
 
 def fwd_bwd_leg(args, peak):
     """The differentiable workload: 16 mixtures (N=2, M=3, L=4, F=257, J=500, B=8, seeds
-    0..15), 20 unrolled iterations with a checkpoint every 5; a step = forward pass, MSE loss
+    0..15), 20 unrolled iterations (by default all of them on the forward pass's tape, one
+    checkpoint segment; --fwdbwd-ckpt sets the segment length); a step = forward pass, MSE loss
     and its gradient, backward pass to X, T0, V0 (all in the library's kernels). Timed with
     CUDA events on the solver's stream; the forward pass alone (with the loss) is timed
     beside it for the fwd+bwd / fwd cost ratio."""
@@ -288,7 +291,8 @@ def fwd_bwd_leg(args, peak):
     sp = specs[0]
     S, K = len(specs), sp.iters
     mixes = [synth.make_mixture(x) for x in specs]
-    g = Grad(sp.M, sp.N, sp.L, sp.B, sp.F, sp.J, batch=S, n_iter=K, ckpt_every=5, Ln=mixes[0].Ln)
+    ckpt = args.fwdbwd_ckpt if args.fwdbwd_ckpt > 0 else K
+    g = Grad(sp.M, sp.N, sp.L, sp.B, sp.F, sp.J, batch=S, n_iter=K, ckpt_every=ckpt, Ln=mixes[0].Ln)
     X = torch.from_numpy(np.stack([m.X for m in mixes])).cuda()
     T0 = torch.from_numpy(np.stack([m.T0 for m in mixes])).cuda()
     V0 = torch.from_numpy(np.stack([m.V0 for m in mixes])).cuda()
@@ -331,7 +335,8 @@ def fwd_bwd_leg(args, peak):
     bytes_it = 6 * y_pass                       # fwd+bwd counted as 6 Y-passes per iteration
     achieved = bytes_it * K / t / 1e9
     return {"workload": f"16 mixtures N={sp.N} M={sp.M} L={sp.L} F={sp.F} J={sp.J} B={sp.B}, {K} unrolled "
-                        "iterations, checkpoint every 5, loss = MSE of the separated images to the true "
+                        f"iterations, checkpoint every {ckpt} (the last segment on the forward pass's tape), "
+                        "loss = MSE of the separated images to the true "
                         "images, gradients to X, T0, V0; seeds 0..15",
             "iterations_per_s": K / t, "bin_frames_per_s": S * sp.F * sp.J * K / t,
             "ms_per_step": ms, "fwd_ms_per_step": ms_fwd, "fwd_bwd_over_fwd": ms / ms_fwd,

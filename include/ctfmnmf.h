@@ -315,8 +315,10 @@ int ctfmnmf_batch_destroy(ctfmnmf_batch_t b);
  * dL/da + i dL/db (PyTorch's). At a floor (T, V or lambda clamped) the gradient through
  * the clamped value is 0; a row with no energy (no normalisation) passes none through mu.
  * Memory: the state (Y, W, T, V) of every mixture is copied every ckpt_every iterations
- * during the forward pass (checkpoints); the backward pass recomputes one segment at a time
- * from its checkpoint, keeping the state of every iteration of that segment.
+ * during the forward pass (checkpoints), and the forward pass keeps the state before every
+ * iteration of its last segment (ckpt_every slots, the tape). The backward pass reverses the
+ * last segment from the tape and recomputes each earlier one from its checkpoint into the same
+ * slots. ckpt_every >= n_iter: one segment, no recomputation, n_iter + 1 states in memory.
  * All device arguments are caller-owned; every call is asynchronous on the object's stream
  * unless stated. Error messages: ctfmnmf_last_error(NULL) on the calling thread.
  */

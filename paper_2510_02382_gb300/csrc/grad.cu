@@ -367,8 +367,11 @@ __global__ void grad_copy_kernel(const Shape s, const StatePtrs* __restrict__ sr
 // ---------------------------------------------------------------- finalize with sigma record
 // As finalize_kernel (the pending normalisation applied to Y, W, log|det|, T, 1/lambda) for every
 // mixture of the batch; also records sigma_r = the applied scale. One block per (bin, mixture)
-// covering all of its rows with 16-byte accesses (two complex values, four 1/lambda).
-__global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* __restrict__ sig)
+// covering all of its rows with 16-byte accesses (two complex values, four 1/lambda). With a
+// snapshot table (snap != NULL) the normalised Y, W, T and a copy of V also go to snap[mixture]:
+// the state at the start of the next iteration, kept for the backward pass.
+__global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* __restrict__ sig,
+                                     const StatePtrs* __restrict__ snap)
 {
     const int i = blockIdx.x, sm = blockIdx.y;
     const Shape& s = mixes[sm].s;
@@ -378,17 +381,23 @@ __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* _
     __shared__ float sc[CTFMNMF_MAX_M];
     if ((int)threadIdx.x < M) sc[threadIdx.x] = d.scale[threadIdx.x];
     __syncthreads();
+    const StatePtrs sp = snap ? snap[sm] : StatePtrs{nullptr, nullptr, nullptr, nullptr};
     const int R4 = Jp >> 1;                              // float4 per row of Y
     float4* Yb = reinterpret_cast<float4*>(d.Y + (size_t)i * M * Jp);
+    float4* Ys = snap ? reinterpret_cast<float4*>(sp.Y + (size_t)i * M * Jp) : nullptr;
     for (int e = threadIdx.x; e < M * R4; e += blockDim.x) {
         const float c = sc[e / R4];
         const float4 v = Yb[e];
-        Yb[e] = make_float4(v.x * c, v.y * c, v.z * c, v.w * c);
+        const float4 o = make_float4(v.x * c, v.y * c, v.z * c, v.w * c);
+        Yb[e] = o;
+        if (Ys) Ys[e] = o;
     }
     if ((int)threadIdx.x < M * M) {
         float2* w = d.W + (size_t)i * M * M + threadIdx.x;
         const float c = sc[threadIdx.x / M];
-        *w = make_float2(w->x * c, w->y * c);
+        const float2 o = make_float2(w->x * c, w->y * c);
+        *w = o;
+        if (snap) sp.W[(size_t)i * M * M + threadIdx.x] = o;
     }
     if (threadIdx.x == 0) {
         double f = d.ldm[i];
@@ -400,7 +409,15 @@ __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* _
     for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
         const int n = t / B, k = t - n * B;
         const float c = sc[s.row0[n]];
-        d.T[(size_t)n * s.FBp + (size_t)i * B + k] *= c * c;
+        const size_t o = (size_t)n * s.FBp + (size_t)i * B + k;
+        const float v = d.T[o] * (c * c);
+        d.T[o] = v;
+        if (snap) sp.T[o] = v;
+    }
+    if (snap) {                                          // V [N][B][Jp], split over the bins
+        const size_t nV4 = (size_t)N * B * Jp / 4;
+        for (size_t e = (size_t)i * blockDim.x + threadIdx.x; e < nV4; e += (size_t)s.F * blockDim.x)
+            reinterpret_cast<float4*>(sp.V)[e] = reinterpret_cast<const float4*>(d.V)[e];
     }
     const int L4 = Jp >> 2;                              // float4 per row of 1/lambda
     float4* il = reinterpret_cast<float4*>(d.invlam + (size_t)i * N * Jp);
@@ -535,9 +552,10 @@ cudaError_t grad_launch_copy(const Shape& s, int S, const StatePtrs* src, const 
     return cudaGetLastError();
 }
 
-cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, float* sig, cudaStream_t st)
+cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, float* sig, cudaStream_t st,
+                                 const StatePtrs* snap)
 {
-    grad_finalize_kernel<<<dim3(s.F, S), 256, 0, st>>>(mixes, sig);
+    grad_finalize_kernel<<<dim3(s.F, S), 256, 0, st>>>(mixes, sig, snap);
     grad_reset_scale_kernel<<<S, 32, 0, st>>>(mixes);
     return cudaGetLastError();
 }

@@ -55,7 +55,9 @@ cudaError_t grad_launch_head(const Shape& s, int S, const StatePtrs* live, const
 cudaError_t grad_launch_inputs(const Shape& s, int S, const StatePtrs* init, const GradBufs& g, int gcur,
                                float2* gX, float* gT0, float* gV0, cudaStream_t st);
 cudaError_t grad_launch_copy(const Shape& s, int S, const StatePtrs* src, const StatePtrs* dst, cudaStream_t st);
-cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, float* sig, cudaStream_t st);
+// snap (device [S], or NULL): also write the normalised state there (the next iteration's start)
+cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, float* sig, cudaStream_t st,
+                                 const StatePtrs* snap = nullptr);
 cudaError_t grad_launch_mse(size_t count, const float2* C, const float2* Cref, double* loss,
                             const double* dloss, float2* gC, cudaStream_t st);
 

@@ -4,12 +4,13 @@
 // is the batched path of batch_api.cpp), the checkpoints, the per-iteration state of one
 // segment, and the gradient buffers of grad.cuh.
 //
-// forward:  load X, T0, V0 -> checkpoint 0 -> for every segment: iterate ckpt_every
-//           iterations, checkpoint -> separated images.
-// backward: images adjoint on the final state; then for segments last .. first: restore the
-//           checkpoint, recompute the segment one iteration at a time (state copied before
-//           each iteration, sigma recorded by the finalize), then reverse its iterations.
-//           Finally the gradients of the first state go to X, T0, V0.
+// forward:  load X, T0, V0 -> checkpoint 0 -> for every segment but the last: iterate
+//           ckpt_every iterations, checkpoint; the last segment one iteration at a time,
+//           keeping the state before each iteration and sigma (the tape) -> separated images.
+// backward: images adjoint on the final state; then for segments last .. first: unless the
+//           segment is on the tape, restore its checkpoint and recompute it one iteration at a
+//           time the same way; then reverse its iterations. Finally the gradients of the
+//           first state go to X, T0, V0.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -41,6 +42,7 @@ struct ctfmnmf_grad {
     float* sig;                  // device [C][S][M]
     std::vector<void*> allocs;
     bool forwarded;
+    bool taped;                  // the iteration slots hold the last segment of the forward pass
     long long launches;
 };
 
@@ -99,6 +101,28 @@ StatePtrs block_ptrs(char* base, const BlockLayout& L)
 
 int seg_len(const ctfmnmf_grad* g, int c) { return c + 1 < g->nseg ? g->C : g->K - c * g->C; }
 
+// Run `len` iterations from the live state one at a time, keeping the state before each one in
+// iteration slot t and the applied normalisation in sigma slot t: slot 0 by a copy, slot t + 1
+// by the finalize of iteration t. Returns the number of launches, or -1 on a launch failure.
+long long record_segment(ctfmnmf_grad* g, int len, cudaStream_t st)
+{
+    const Shape& s = g->s;
+    const int S = g->S;
+    const StatePtrs* live = g->tab + (size_t)g->C * S;
+    if (ctf::grad_launch_copy(s, S, live, g->tab, st) != cudaSuccess) return -1;
+    long long n = 1;
+    for (int t = 0; t < len; ++t) {
+        const StatePtrs* snap = t + 1 < len ? g->tab + (size_t)(t + 1) * S : nullptr;
+        if (ctf::batch_enqueue(g->batch, 1, st) != cudaSuccess ||
+            ctf::grad_launch_finalize(s, S, g->mix, g->sig + (size_t)t * S * s.M, st, snap) != cudaSuccess)
+            return -1;
+        n += 2;
+    }
+    int info[5] = {0, 0, 0, 0, 0};
+    ctfmnmf_batch_info(g->batch, info);
+    return n + (long long)len * (info[1] + info[2]);
+}
+
 void release(ctfmnmf_grad* g)
 {
     if (g->batch) ctfmnmf_batch_destroy(g->batch);
@@ -146,6 +170,7 @@ int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int 
     g->mix = nullptr;
     g->sig = nullptr;
     g->forwarded = false;
+    g->taped = false;
     g->launches = 0;
     memset(&g->g, 0, sizeof(g->g));
     ctfmnmf_options opt;
@@ -250,17 +275,20 @@ int ctfmnmf_grad_forward(ctfmnmf_grad_t g, const void* X, const float* T0, const
     if (ctf::grad_launch_copy(s, S, g->tab + (size_t)g->C * S, g->ck, st) != cudaSuccess)
         return gfail(CTFMNMF_ECUDA, "checkpoint copy failed");
     ++g->launches;
+    g->taped = false;
     const long long b0 = batch_launches(g->batch);
-    for (int c = 0; c < g->nseg; ++c) {
+    for (int c = 0; c + 1 < g->nseg; ++c) {
         const int rc = ctfmnmf_batch_iterate(g->batch, seg_len(g, c));
         if (rc != CTFMNMF_OK) return rc;
-        if (c + 1 < g->nseg) {
-            if (ctf::grad_launch_copy(s, S, g->tab + (size_t)g->C * S, g->ck + (size_t)(c + 1) * S, st) != cudaSuccess)
-                return gfail(CTFMNMF_ECUDA, "checkpoint copy failed");
-            ++g->launches;
-        }
+        if (ctf::grad_launch_copy(s, S, g->tab + (size_t)g->C * S, g->ck + (size_t)(c + 1) * S, st) != cudaSuccess)
+            return gfail(CTFMNMF_ECUDA, "checkpoint copy failed");
+        ++g->launches;
     }
     g->launches += batch_launches(g->batch) - b0;
+    const long long nrec = record_segment(g, seg_len(g, g->nseg - 1), st);
+    if (nrec < 0) return gfail(CTFMNMF_ECUDA, "the last segment's iterations failed");
+    g->launches += nrec;
+    g->taped = true;
     for (int k = 0; k < S; ++k) {
         ctfmnmf* h = g->hs[k];
         float2* Ck = static_cast<float2*>(C) + (size_t)k * s.N * s.M * s.F * s.J;
@@ -292,23 +320,20 @@ int ctfmnmf_grad_backward(ctfmnmf_grad_t g, const void* gC, void* gX, float* gT0
     int gcur = 0;
     // the forward state is consumed from here on: a second backward needs a new forward
     g->forwarded = false;
+    const bool taped = g->taped;
+    g->taped = false;
     for (int c = g->nseg - 1; c >= 0; --c) {
         const int len = seg_len(g, c);
-        if (ctf::grad_launch_copy(s, S, g->ck + (size_t)c * S, g->tab + (size_t)g->C * S, st) != cudaSuccess)
-            return gfail(CTFMNMF_ECUDA, "restoring checkpoint %d failed", c);
-        for (ctfmnmf_t h : g->hs)
-            if (ctf::launch_psd(h->s, h->d, st) != cudaSuccess) return gfail(CTFMNMF_ECUDA, "psd launch failed");
-        n += 1 + S;
-        for (int t = 0; t < len; ++t) {
-            if (ctf::grad_launch_copy(s, S, live, g->tab + (size_t)t * S, st) != cudaSuccess ||
-                ctf::batch_enqueue(g->batch, 1, st) != cudaSuccess ||
-                ctf::grad_launch_finalize(s, S, g->mix, g->sig + (size_t)t * S * M, st) != cudaSuccess)
-                return gfail(CTFMNMF_ECUDA, "recomputing iteration %d of segment %d failed", t, c);
-            n += 3;
+        if (!(taped && c == g->nseg - 1)) {
+            if (ctf::grad_launch_copy(s, S, g->ck + (size_t)c * S, g->tab + (size_t)g->C * S, st) != cudaSuccess)
+                return gfail(CTFMNMF_ECUDA, "restoring checkpoint %d failed", c);
+            for (ctfmnmf_t h : g->hs)
+                if (ctf::launch_psd(h->s, h->d, st) != cudaSuccess) return gfail(CTFMNMF_ECUDA, "psd launch failed");
+            n += 1 + S;
+            const long long nrec = record_segment(g, len, st);
+            if (nrec < 0) return gfail(CTFMNMF_ECUDA, "recomputing segment %d failed", c);
+            n += nrec;
         }
-        int info[5] = {0, 0, 0, 0, 0};
-        ctfmnmf_batch_info(g->batch, info);
-        n += (long long)len * (info[1] + info[2]);
         for (int t = len - 1; t >= 0; --t) {
             GradBufs gi = g->g;
             gi.sig = g->sig + (size_t)t * S * M;

@@ -23,6 +23,7 @@ SHAPES = [
     (4, 3, (2, 1, 1), 6, 70, 5, 6, 4, 2),
     (3, 2, (2, 1), 4, 700, 10, 3, 2, 1),      # two frames per thread, several frame tiles
     (3, 2, (2, 1), 3, 130, 20, 2, 1, 3),      # B > 16, a checkpoint every iteration
+    (3, 2, (2, 1), 7, 45, 6, 5, 8, 2),        # one segment: every iteration on the forward tape
 ]
 
 
@@ -96,6 +97,19 @@ def test_directional_derivatives_match_oracle_differences():
         d = rng.standard_normal(V0.shape)
         fd = (loss(X, T0, V0 + 1e-6 * d) - loss(X, T0, V0 - 1e-6 * d)) / 2e-6
         assert abs(np.sum(out["gV0"][k] * d) - fd) <= TOL * abs(fd)
+
+
+def test_tape_and_recomputation_agree():
+    """One segment (every state from the forward pass's tape) against a checkpoint every
+    iteration (all but the last iteration recomputed in the backward pass): the same gradients
+    up to the rounding of the recomputed 1/lambda."""
+    M, N, Ln, F, J, B, K, C, S = SHAPES[0]
+    mixes = _batch(SHAPES[0])
+    taped = _run((M, N, Ln, F, J, B, K, K, S), mixes)
+    recomputed = _run((M, N, Ln, F, J, B, K, 1, S), mixes)
+    assert abs(taped["loss"] - recomputed["loss"]) <= 1e-6 * abs(taped["loss"])
+    for key in ("C", "gX", "gT0", "gV0"):
+        assert rel_fro(taped[key], recomputed[key]) < 1e-4, key
 
 
 def test_autograd_function_matches_direct_calls():
