@@ -3,7 +3,9 @@
 //
 // Per iteration t, in stream order:
 //   A grad_norm_kernel     (bin, mixture)          e_r = sum Re(conj(gY') Y') + Re(conj(gW') W')
-//                                                  + [l(r) = 0] 2 sum gT' T'   (the sigma sums)
+//                                                  + [l(r) = 0] 2 sum gT' T'   (the sigma sums);
+//                                                  only for the first iteration reversed: kernel C
+//                                                  forms the sums of the iteration before its own
 //   B grad_vmu_kernel      (128 frames, source, mixture)  denV by a sweep over all bins; from
 //                                                  dL/dV' the gradients of numV, denV and the
 //                                                  direct part V' = V R of dL/dV
@@ -497,16 +499,22 @@ cudaError_t grad_configure(const Shape& s)
 }
 
 cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt,
-                                   const GradBufs& g, int gin, cudaStream_t st)
+                                   const GradBufs& g, int gin, bool first, cudaStream_t st, int* kernels)
 {
-    cudaError_t e = cudaMemsetAsync(g.e, 0, sizeof(double) * S * s.M, st);
-    if (e != cudaSuccess) return e;
-    switch (s.M) {
-        case 2: grad_norm_kernel<2><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
-        case 3: grad_norm_kernel<3><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
-        case 4: grad_norm_kernel<4><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
-        default: return cudaErrorInvalidValue;
+    *kernels = 3;
+    if (first) {
+        cudaError_t e = cudaMemsetAsync(g.e, 0, sizeof(double) * S * s.M, st);
+        if (e != cudaSuccess) return e;
+        switch (s.M) {
+            case 2: grad_norm_kernel<2><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
+            case 3: grad_norm_kernel<3><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
+            case 4: grad_norm_kernel<4><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
+            default: return cudaErrorInvalidValue;
+        }
+        *kernels = 4;
     }
+    cudaError_t e = cudaMemsetAsync(g.e_prev, 0, sizeof(double) * S * s.M, st);
+    if (e != cudaSuccess) return e;
     const dim3 fgrid((s.Jp + kGradTile - 1) / kGradTile, s.N, S);
     switch (pick_bb(s.B)) {
         case 4: grad_vmu_kernel<4><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;

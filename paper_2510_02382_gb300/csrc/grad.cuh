@@ -40,16 +40,20 @@ struct GradBufs {
     float* aq;           // [S][N][F][Jp]  A = (delayed power) / lambda^2 of the basis MU
     float* gnT;          // [S][N][FBp]    dL/d numT (basis MU numerator)
     float* gdT;          // [S][N][FBp]    dL/d denT
-    double* e;           // [S][M]         normalisation sums (see grad_norm_kernel)
+    double* e;           // [S][M]         normalisation sums of the iteration being reversed
+                         //                (grad_norm_kernel, or the previous reversed iteration)
+    double* e_prev;      // [S][M]         the same sums of the iteration before it, accumulated by
+                         //                the per-bin adjoint from its outputs (zeroed before it)
     const float* sig;    // [S][M]         sigma_r of the iteration being reversed
 };
 
 cudaError_t grad_configure(const Shape& s);
 // Enqueue the backward pass of one iteration (kernels A-D of grad.cu); gin selects the
-// gV buffer that holds dL/dV'; the other receives dL/dV.
+// gV buffer that holds dL/dV'; the other receives dL/dV. first: the first iteration reversed,
+// whose normalisation sums kernel A forms (later ones get them from the per-bin adjoint of the
+// iteration reversed before, in g.e). Returns the kernels launched in *kernels.
 cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt,
-                                   const GradBufs& g, int gin, cudaStream_t st);
-constexpr int kGradIterationKernels = 4;   // plus one memset
+                                   const GradBufs& g, int gin, bool first, cudaStream_t st, int* kernels);
 cudaError_t grad_launch_head(const Shape& s, int S, const StatePtrs* live, const float2* gC, const GradBufs& g,
                              cudaStream_t st);
 cudaError_t grad_launch_inputs(const Shape& s, int S, const StatePtrs* init, const GradBufs& g, int gcur,

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "grad.cuh"
@@ -203,7 +204,7 @@ int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int 
               dalloc(g, &gb.gV[0], nV) && dalloc(g, &gb.gV[1], nV) && dalloc(g, &gb.gnum, nV) &&
               dalloc(g, &gb.gden, nV) && dalloc(g, &gb.glp, nL) && dalloc(g, &gb.glt, nL) &&
               dalloc(g, &gb.aq, nL) && dalloc(g, &gb.gnT, nT) && dalloc(g, &gb.gdT, nT) &&
-              dalloc(g, &gb.e, (size_t)S * M);
+              dalloc(g, &gb.e, (size_t)S * M) && dalloc(g, &gb.e_prev, (size_t)S * M);
     if (!ok) {
         release(g);
         return gfail(CTFMNMF_ENOMEM, "device allocation of the differentiable form failed");
@@ -317,7 +318,8 @@ int ctfmnmf_grad_backward(ctfmnmf_grad_t g, const void* gC, void* gX, float* gT0
         cudaMemsetAsync(gb.gV[0], 0, sizeof(float) * (size_t)S * s.N * s.B * s.Jp, st) != cudaSuccess)
         return gfail(CTFMNMF_ECUDA, "images adjoint failed");
     long long n = 1;
-    int gcur = 0;
+    int gcur = 0, ecur = 0;
+    bool first = true;
     // the forward state is consumed from here on: a second backward needs a new forward
     g->forwarded = false;
     const bool taped = g->taped;
@@ -337,12 +339,16 @@ int ctfmnmf_grad_backward(ctfmnmf_grad_t g, const void* gC, void* gX, float* gT0
         for (int t = len - 1; t >= 0; --t) {
             GradBufs gi = g->g;
             gi.sig = g->sig + (size_t)t * S * M;
+            if (ecur) std::swap(gi.e, gi.e_prev);      // the sums written by the previous iteration
             const StatePtrs* cur = g->tab + (size_t)t * S;
             const StatePtrs* nxt = t + 1 == len ? live : g->tab + (size_t)(t + 1) * S;
-            if (ctf::grad_enqueue_iteration(s, S, cur, nxt, gi, gcur, st) != cudaSuccess)
+            int kernels = 0;
+            if (ctf::grad_enqueue_iteration(s, S, cur, nxt, gi, gcur, first, st, &kernels) != cudaSuccess)
                 return gfail(CTFMNMF_ECUDA, "backward of iteration %d of segment %d failed", t, c);
             gcur = 1 - gcur;
-            n += ctf::kGradIterationKernels;
+            ecur = 1 - ecur;
+            first = false;
+            n += kernels;
         }
     }
     if (ctf::grad_launch_inputs(s, S, g->ck, g->g, gcur, static_cast<float2*>(gX), gT0, gV0, st) != cudaSuccess)

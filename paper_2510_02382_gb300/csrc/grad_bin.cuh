@@ -66,6 +66,7 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     __shared__ float2 gn_b[M];
     __shared__ float gd_b[M];
     __shared__ float gq_b;
+    __shared__ float eas[16 * M];                          // per-warp sums of Re(conj(dL/dY) Y)
 
     const int i = blockIdx.x, sm = blockIdx.y;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
@@ -91,18 +92,8 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         const float2 gw = g.gW[(((size_t)sm * F + i) * M + p) * M + c];
         gWs[p][c] = make_float2(gw.x * sig[p], gw.y * sig[p]);
     }
-    __syncthreads();
-    // ---- 1/lambda of the iteration's T, V; the rows at the start of the iteration
-    for (int e = tid; e < N * Jp; e += NT) {
-        const int n = e / Jp, j = e - n * Jp;
-        float v = 0.f;
-        if (j < J) {
-            float lam = 0.f;
-            for (int k = 0; k < B; ++k) lam = fmaf(Ti[n * B + k], cur.V[((size_t)n * B + k) * Jp + j], lam);
-            v = 1.f / fmaxf(lam, kFloorPsd);
-        }
-        invl[e] = v;
-    }
+    // ---- the rows at the start of the iteration; V (when staged); then 1/lambda of the
+    // iteration's T, V from the staged copy
     {
         const float2* Yc = cur.Y + (size_t)i * M * Jp;
         for (int e = tid; e < M * Jp; e += NT) y0s[e] = Yc[e];
@@ -112,6 +103,17 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     }
     __syncthreads();
     const float* Vsrc = vstage ? Vst : cur.V;              // V [N][B][Jp], shared or global
+    for (int e = tid; e < N * Jp; e += NT) {
+        const int n = e / Jp, j = e - n * Jp;
+        float v = 0.f;
+        if (j < J) {
+            float lam = 0.f;
+            for (int k = 0; k < B; ++k) lam = fmaf(Ti[n * B + k], Vsrc[((size_t)n * B + k) * Jp + j], lam);
+            v = 1.f / fmaxf(lam, kFloorPsd);
+        }
+        invl[e] = v;
+    }
+    __syncthreads();
     const float thr = 1.f / kFloorPsd;                     // 1/lambda at (or past) the floor
 
     auto phi = [&](int p, int j) -> float {   // 1/lambda_{n(p), j - l(p)}, 0 when masked
@@ -472,16 +474,30 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         }
     }
 
-    // ---- outputs: dL/dY, dL/dW of the iteration start
+    // ---- outputs: dL/dY, dL/dW of the iteration start; eas: the warps' parts of
+    // sum_j Re(conj(dL/dY) Y) (the sigma sums of the iteration before, completed at the end)
     {
+        float ea[M];
         float2* gYo = g.gY + ((size_t)sm * F + i) * M * Jp;
 #pragma unroll
-        for (int r = 0; r < M; ++r)
+        for (int r = 0; r < M; ++r) {
+            ea[r] = 0.f;
 #pragma unroll
             for (int f = 0; f < FPT; ++f) {
                 const int j = tid + f * NT;
+                if (j < J) {
+                    const float2 y = y0s[r * Jp + j];
+                    ea[r] = fmaf(gy[r][f].x, y.x, fmaf(gy[r][f].y, y.y, ea[r]));
+                }
                 if (j < Jp) gYo[(size_t)r * Jp + j] = j < J ? gy[r][f] : make_float2(0.f, 0.f);
             }
+        }
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ea[r] += __shfl_xor_sync(0xffffffffu, ea[r], o);
+            if (lane == 0) eas[(tid >> 5) * M + r] = ea[r];
+        }
         if (tid < M * M) {
             const int p = tid / M, c = tid - p * M;
             g.gW[(((size_t)sm * F + i) * M + p) * M + c] = gWs[p][c];
@@ -541,6 +557,30 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     for (int t = tid; t < N * B; t += NT) {
         const int n = t / B, k = t - n * B;
         g.gT[tb + (size_t)n * FBp + (size_t)i * B + k] = gTacc[t];
+    }
+    // ---- the sigma sums of the iteration before this one (whose result is this iteration's
+    // start state and dL/d of it the outputs above): e_r = sum_j Re(conj(dL/dY) Y)
+    // + sum_c Re(conj(dL/dW) W) + [r = (n, 0)] 2 sum_k dL/dT T
+    {
+        float a[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) a[r] = tid < (NT >> 5) ? eas[tid * M + r] : 0.f;
+        if (tid < M * M) {
+            const int p = tid / M, c = tid - p * M;
+            const float w = gWs[p][c].x * Wv[0][p][c].x + gWs[p][c].y * Wv[0][p][c].y;
+#pragma unroll
+            for (int r = 0; r < M; ++r)
+                if (r == p) a[r] += w;
+        }
+        for (int t = tid; t < N * B; t += NT) {
+            const int r0 = s.row0[t / B];
+            const float v = 2.f * gTacc[t] * Ti[t];
+#pragma unroll
+            for (int r = 0; r < M; ++r)
+                if (r == r0) a[r] += v;
+        }
+        block_sum<M>(a, red, bout);
+        if (tid < M) atomicAdd(&g.e_prev[sm * M + tid], (double)bout[tid]);
     }
 }
 
