@@ -6,7 +6,7 @@
 //                                                  + [l(r) = 0] 2 sum gT' T'   (the sigma sums);
 //                                                  only for the first iteration reversed: kernel C
 //                                                  forms the sums of the iteration before its own
-//   B grad_vmu_kernel      (128 frames, source, mixture)  denV by a sweep over all bins; from
+//   B grad_vmu_kernel      (32 frames, source, mixture)  denV by a sweep over all bins; from
 //                                                  dL/dV' the gradients of numV, denV and the
 //                                                  direct part V' = V R of dL/dV
 //   C grad_bin_kernel      (bin, mixture)          recompute the ISS sweep; adjoint of the
@@ -63,15 +63,23 @@ __global__ void __launch_bounds__(256) grad_norm_kernel(const Shape s, const Sta
 }
 
 // ---------------------------------------------------------------- B: activation-MU gradients
+// Block = kVT frames x kVG bin groups: warp w sums the bins i = w mod kVG for its lane's frame,
+// then the groups' partial denominators are added in shared memory and each warp finishes
+// the bases k = w mod kVG.
+constexpr int kVT = 32;    // frames per block (one per lane)
+constexpr int kVG = 8;     // bin groups per block (one per warp)
 constexpr int kIC = 256;   // bins staged per pass
 
 template <int BB>
-__global__ void __launch_bounds__(kGradTile) grad_vmu_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
+__global__ void __launch_bounds__(kVT * kVG) grad_vmu_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
                                                              const StatePtrs* __restrict__ nxt_tab, const GradBufs g,
                                                              const int gin)
 {
-    __shared__ float T1s[kIC * BB];
-    const int sm = blockIdx.z, n = blockIdx.y, j = blockIdx.x * kGradTile + threadIdx.x;
+    constexpr int kSh = kIC * BB > kVG * BB * kVT ? kIC * BB : kVG * BB * kVT;
+    __shared__ float sh[kSh];                          // T1 of kIC bins, then the partial denominators
+    const int sm = blockIdx.z, n = blockIdx.y;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int j = blockIdx.x * kVT + lane;
     const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp;
     const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
     const float s0 = g.sig[sm * s.M + s.row0[n]];
@@ -89,12 +97,12 @@ __global__ void __launch_bounds__(kGradTile) grad_vmu_kernel(const Shape s, cons
         __syncthreads();
         for (int e = threadIdx.x; e < ic * BB; e += blockDim.x) {
             const int ii = e / BB, k = e - ii * BB;
-            T1s[e] = k < B ? nxt.T[(size_t)n * FBp + (size_t)(i0 + ii) * B + k] * inv : 0.f;
+            sh[e] = k < B ? nxt.T[(size_t)n * FBp + (size_t)(i0 + ii) * B + k] * inv : 0.f;
         }
         __syncthreads();
         if (live) {
-            for (int ii = 0; ii < ic; ++ii) {
-                const float* t1 = T1s + ii * BB;
+            for (int ii = grp; ii < ic; ii += kVG) {
+                const float* t1 = sh + ii * BB;
                 float lam = 0.f;
 #pragma unroll
                 for (int k = 0; k < BB; ++k) lam = fmaf(t1[k], v[k], lam);
@@ -104,21 +112,26 @@ __global__ void __launch_bounds__(kGradTile) grad_vmu_kernel(const Shape s, cons
             }
         }
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BB; ++k) sh[(grp * BB + k) * kVT + lane] = den[k];
+    __syncthreads();
     if (j >= Jp) return;
     const size_t base = ((size_t)sm * N + n) * B * (size_t)Jp + j;
+    for (int k = grp; k < B; k += kVG) {
+        float dk = 0.f;
 #pragma unroll
-    for (int k = 0; k < BB; ++k) {
-        if (k >= B) break;
+        for (int q = 0; q < kVG; ++q) dk += sh[(q * BB + k) * kVT + lane];
         const size_t idx = base + (size_t)k * Jp;
         float gn = 0.f, gd = 0.f, gv = 0.f;
         if (live) {
             const float g1 = g.gV[gin][idx];
-            const float V1 = nxt.V[((size_t)n * B + k) * Jp + j], V = v[k];
-            if (V1 > s.floor_nmf && V > 0.f && den[k] > 0.f) {
+            const float V1 = nxt.V[((size_t)n * B + k) * Jp + j], V = cur.V[((size_t)n * B + k) * Jp + j];
+            if (V1 > s.floor_nmf && V > 0.f && dk > 0.f) {
                 // V1 = V R, R = sqrt(numV / denV): dR/dnum = 1/(2 R den), dR/dden = -R/(2 den)
                 const float R = V1 / V, gR = g1 * V;
-                gn = gR / (2.f * R * den[k]);
-                gd = -gR * R / (2.f * den[k]);
+                gn = gR / (2.f * R * dk);
+                gd = -gR * R / (2.f * dk);
                 gv = g1 * R;
             }
         }
@@ -515,13 +528,14 @@ cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, 
     }
     cudaError_t e = cudaMemsetAsync(g.e_prev, 0, sizeof(double) * S * s.M, st);
     if (e != cudaSuccess) return e;
-    const dim3 fgrid((s.Jp + kGradTile - 1) / kGradTile, s.N, S);
+    const dim3 vgrid((s.Jp + kVT - 1) / kVT, s.N, S);
     switch (pick_bb(s.B)) {
-        case 4: grad_vmu_kernel<4><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
-        case 8: grad_vmu_kernel<8><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
-        case 16: grad_vmu_kernel<16><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
-        default: grad_vmu_kernel<32><<<fgrid, kGradTile, 0, st>>>(s, cur, nxt, g, gin); break;
+        case 4: grad_vmu_kernel<4><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
+        case 8: grad_vmu_kernel<8><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
+        case 16: grad_vmu_kernel<16><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
+        default: grad_vmu_kernel<32><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
     }
+    const dim3 fgrid((s.Jp + kGradTile - 1) / kGradTile, s.N, S);
     e = launch_bin(s, S, cur, nxt, g, st, false);
     if (e != cudaSuccess) return e;
     const dim3 dgrid(fgrid.x * ((s.F + kID - 1) / kID), s.N, S);

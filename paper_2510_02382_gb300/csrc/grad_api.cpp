@@ -45,6 +45,15 @@ struct ctfmnmf_grad {
     bool forwarded;
     bool taped;                  // the iteration slots hold the last segment of the forward pass
     long long launches;
+    // CUDA graphs of the fixed launch sequences, captured on first use on a private stream and
+    // replayed on the object's stream: a recorded segment by length (the checkpoint length and
+    // the last segment's), the reverse pass of each segment; with their kernel counts
+    cudaStream_t cap;
+    cudaGraphExec_t rec_graph[2];
+    int rec_len[2];
+    long long rec_kernels[2];
+    std::vector<cudaGraphExec_t> rev_graph;
+    std::vector<long long> rev_kernels;
 };
 
 namespace {
@@ -102,10 +111,36 @@ StatePtrs block_ptrs(char* base, const BlockLayout& L)
 
 int seg_len(const ctfmnmf_grad* g, int c) { return c + 1 < g->nseg ? g->C : g->K - c * g->C; }
 
+// Capture enqueue(stream) -> kernel count (< 0: failure) into *slot on the capture stream once,
+// then launch the graph on st. Returns the kernel count, or -1.
+template <class Fn>
+long long graph_run(ctfmnmf_grad* g, cudaGraphExec_t* slot, long long* kernels, Fn enqueue, cudaStream_t st)
+{
+    if (!*slot) {
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1;
+        const long long n = enqueue(g->cap);
+        const cudaError_t ec = cudaStreamEndCapture(g->cap, &gr);
+        if (n < 0 || ec != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return -1;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(slot, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ei != cudaSuccess) {
+            *slot = nullptr;
+            return -1;
+        }
+        *kernels = n;
+    }
+    return cudaGraphLaunch(*slot, st) == cudaSuccess ? *kernels : -1;
+}
+
 // Run `len` iterations from the live state one at a time, keeping the state before each one in
 // iteration slot t and the applied normalisation in sigma slot t: slot 0 by a copy, slot t + 1
 // by the finalize of iteration t. Returns the number of launches, or -1 on a launch failure.
-long long record_segment(ctfmnmf_grad* g, int len, cudaStream_t st)
+long long record_segment_direct(ctfmnmf_grad* g, int len, cudaStream_t st)
 {
     const Shape& s = g->s;
     const int S = g->S;
@@ -124,8 +159,24 @@ long long record_segment(ctfmnmf_grad* g, int len, cudaStream_t st)
     return n + (long long)len * (info[1] + info[2]);
 }
 
+// record_segment_direct through a graph per segment length
+long long record_segment(ctfmnmf_grad* g, int len, cudaStream_t st)
+{
+    int k = 0;
+    while (k < 2 && g->rec_graph[k] && g->rec_len[k] != len) ++k;
+    if (k == 2) return record_segment_direct(g, len, st);   // not expected: two lengths at most
+    g->rec_len[k] = len;
+    return graph_run(g, &g->rec_graph[k], &g->rec_kernels[k],
+                     [&](cudaStream_t cs) { return record_segment_direct(g, len, cs); }, st);
+}
+
 void release(ctfmnmf_grad* g)
 {
+    for (int k = 0; k < 2; ++k)
+        if (g->rec_graph[k]) cudaGraphExecDestroy(g->rec_graph[k]);
+    for (cudaGraphExec_t x : g->rev_graph)
+        if (x) cudaGraphExecDestroy(x);
+    if (g->cap) cudaStreamDestroy(g->cap);
     if (g->batch) ctfmnmf_batch_destroy(g->batch);
     for (ctfmnmf_t h : g->hs) ctfmnmf_destroy(h);
     for (void* p : g->allocs) cudaFree(p);
@@ -173,6 +224,14 @@ int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int 
     g->forwarded = false;
     g->taped = false;
     g->launches = 0;
+    g->cap = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        g->rec_graph[k] = nullptr;
+        g->rec_len[k] = 0;
+        g->rec_kernels[k] = 0;
+    }
+    g->rev_graph.assign(g->nseg, nullptr);
+    g->rev_kernels.assign(g->nseg, 0);
     memset(&g->g, 0, sizeof(g->g));
     ctfmnmf_options opt;
     ctfmnmf_default_options(&opt);
@@ -227,6 +286,12 @@ int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int 
         cudaGetLastError();
         release(g);
         return gfail(CTFMNMF_ECUDA, "copying the state tables to the device failed");
+    }
+    if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        g->cap = nullptr;
+        release(g);
+        return gfail(CTFMNMF_ECUDA, "creating the capture stream failed");
     }
     const cudaError_t e = ctf::grad_configure(s);
     if (e != cudaSuccess) {
@@ -336,20 +401,37 @@ int ctfmnmf_grad_backward(ctfmnmf_grad_t g, const void* gC, void* gX, float* gT0
             if (nrec < 0) return gfail(CTFMNMF_ECUDA, "recomputing segment %d failed", c);
             n += nrec;
         }
-        for (int t = len - 1; t >= 0; --t) {
-            GradBufs gi = g->g;
-            gi.sig = g->sig + (size_t)t * S * M;
-            if (ecur) std::swap(gi.e, gi.e_prev);      // the sums written by the previous iteration
-            const StatePtrs* cur = g->tab + (size_t)t * S;
-            const StatePtrs* nxt = t + 1 == len ? live : g->tab + (size_t)(t + 1) * S;
-            int kernels = 0;
-            if (ctf::grad_enqueue_iteration(s, S, cur, nxt, gi, gcur, first, st, &kernels) != cudaSuccess)
-                return gfail(CTFMNMF_ECUDA, "backward of iteration %d of segment %d failed", t, c);
+        // the reverse pass of the segment: a fixed sequence for a given segment (the buffer
+        // parities and `first` follow from the iterations reversed before it)
+        const int gcur0 = gcur, ecur0 = ecur;
+        const bool first0 = first;
+        auto reverse = [&](cudaStream_t rs) -> long long {
+            int gc = gcur0, ec = ecur0;
+            bool fst = first0;
+            long long nk = 0;
+            for (int t = len - 1; t >= 0; --t) {
+                GradBufs gi = g->g;
+                gi.sig = g->sig + (size_t)t * S * M;
+                if (ec) std::swap(gi.e, gi.e_prev);    // the sums written by the previous iteration
+                const StatePtrs* cur = g->tab + (size_t)t * S;
+                const StatePtrs* nxt = t + 1 == len ? live : g->tab + (size_t)(t + 1) * S;
+                int kernels = 0;
+                if (ctf::grad_enqueue_iteration(s, S, cur, nxt, gi, gc, fst, rs, &kernels) != cudaSuccess) return -1;
+                gc = 1 - gc;
+                ec = 1 - ec;
+                fst = false;
+                nk += kernels;
+            }
+            return nk;
+        };
+        const long long nrev = graph_run(g, &g->rev_graph[c], &g->rev_kernels[c], reverse, st);
+        if (nrev < 0) return gfail(CTFMNMF_ECUDA, "backward of segment %d failed", c);
+        n += nrev;
+        if (len & 1) {
             gcur = 1 - gcur;
             ecur = 1 - ecur;
-            first = false;
-            n += kernels;
         }
+        first = false;
     }
     if (ctf::grad_launch_inputs(s, S, g->ck, g->g, gcur, static_cast<float2*>(gX), gT0, gV0, st) != cudaSuccess)
         return gfail(CTFMNMF_ECUDA, "input gradients failed");
