@@ -9,6 +9,10 @@
 //   B grad_vmu_kernel      (32 frames, source, mixture)  denV by a sweep over all bins; from
 //                                                  dL/dV' the gradients of numV, denV and the
 //                                                  direct part V' = V R of dL/dV
+//   E grad_act_kernel      (256 frames x 32 bins, source, mixture)  the activation MU's
+//                                                  per-bin adjoint parts (dL/dlambda', dL/dS,
+//                                                  per-tile sums of dL/dT1 and the basis-MU
+//                                                  denominator)
 //   C grad_bin_kernel      (bin, mixture)          recompute the ISS sweep; adjoint of the
 //                                                  normalisation, the activation MU (per-bin
 //                                                  parts), the basis MU and the ISS sweep;
@@ -140,6 +144,123 @@ __global__ void __launch_bounds__(kVT * kVG) grad_vmu_kernel(const Shape s, cons
         g.gV[1 - gin][idx] = gv;
     }
 }
+
+// ---------------------------------------------------------------- E: activation-MU adjoint, per-bin parts
+// For every (bin i, frame j) of one (source n, mixture): with T1 = T'/sigma_{(n,0)}^2, the
+// delayed power S of |Y1|^2 = |Y'|^2 / sigma^2 over the source's taps, c the tap count and
+// lambda' = T1 V: A = S / lambda'^2, dL/dlambda' = -2 A gA / lambda' - c gC / lambda'^2
+// (0 where lambda' is floored) with gA = sum_k dL/dnumV T1, gC = sum_k dL/ddenV T1, and
+// dL/dS = gA / lambda'^2; per bin the sums over frames of dL/dT1 (sum_j dL/dnumV A +
+// dL/ddenV c/lambda' + dL/dlambda' V) and of the basis-MU denominator (sum_j V c/lambda with
+// lambda = T V). Block = kEW warps x 32 frames (one frame per lane) over kEI bins; V and the
+// two gradient planes of its frames are staged once in shared memory for all of its bins.
+// The per-bin sums go out per 32-frame tile (actp), added up by grad_bin_kernel.
+constexpr int kEW = 8;     // warps (32-frame tiles) per block
+constexpr int kEI = 32;    // bins per block
+
+__global__ void __launch_bounds__(kEW * 32) grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
+                                                            const StatePtrs* __restrict__ nxt_tab, const GradBufs g)
+{
+    extern __shared__ float esm[];
+    constexpr int FT = kEW * 32;                       // frames per block
+    const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp, M = s.M;
+    const int sm = blockIdx.z / N, n = blockIdx.z - sm * N;
+    const int j0 = blockIdx.x * FT, i0 = blockIdx.y * kEI;
+    const int ic = min(kEI, F - i0);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float* Vt = esm;                                   // [B][FT]
+    float* Gn = Vt + B * FT;                           // [B][FT]
+    float* Gd = Gn + B * FT;                           // [B][FT]
+    float* T1s = Gd + B * FT;                          // [kEI][B]
+    float* Ts = T1s + kEI * B;                         // [kEI][B]
+    const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
+    const float* sig = g.sig + sm * M;
+    const int r0 = s.row0[n], Lq = s.Ln[n];
+    const float s0 = sig[r0];
+    const float inv = 1.f / (s0 * s0);
+    const size_t pl = ((size_t)sm * N + n) * B * (size_t)Jp;     // [S][N][B][Jp] planes
+    for (int e = tid; e < B * FT; e += blockDim.x) {
+        const int k = e / FT, jj = e - k * FT, j = j0 + jj;
+        float v = 0.f, gn = 0.f, gd = 0.f;
+        if (j < J) {
+            const size_t o = (size_t)k * Jp + j;
+            v = cur.V[(size_t)n * B * Jp + o];
+            gn = g.gnum[pl + o];
+            gd = g.gden[pl + o];
+        }
+        Vt[e] = v;
+        Gn[e] = gn;
+        Gd[e] = gd;
+    }
+    for (int e = tid; e < ic * B; e += blockDim.x) {
+        const size_t o = (size_t)n * FBp + (size_t)i0 * B + e;       // bins i0.. are contiguous
+        T1s[e] = nxt.T[o] * inv;
+        Ts[e] = cur.T[o];
+    }
+    __syncthreads();
+    if (j0 + w * 32 >= Jp) return;                     // a warp past the last frame tile
+    const int jj = w * 32 + lane, j = j0 + jj;
+    const bool live = j < J;
+    const float c = live ? (float)min(Lq, J - j) : 0.f;
+    float isg[kGradMaxM];                              // 1 / sigma^2 of the source's rows
+#pragma unroll
+    for (int l = 0; l < kGradMaxM; ++l) {
+        const float sg = l < Lq ? sig[r0 + l] : 0.f;
+        isg[l] = sg > 0.f ? 1.f / (sg * sg) : 0.f;
+    }
+    const int tiles = (Jp + 31) >> 5, tile = (j0 >> 5) + w;
+    for (int ii = 0; ii < ic; ++ii) {
+        const int i = i0 + ii;
+        float A = 0.f, cc = 0.f, gp = 0.f, gs = 0.f, ci = 0.f;
+        if (live) {
+            const float2* Yb = nxt.Y + (size_t)i * M * Jp;
+            float S = 0.f;
+#pragma unroll
+            for (int l = 0; l < kGradMaxM; ++l)
+                if (l < Lq && j + l < J) S = fmaf(abs2(Yb[(size_t)(r0 + l) * Jp + j + l]), isg[l], S);
+            const float* t1 = T1s + ii * B;
+            const float* t = Ts + ii * B;
+            float raw = 0.f, gA = 0.f, gC = 0.f, lam = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < B; ++k) {
+                const float v = Vt[k * FT + jj];
+                raw = fmaf(t1[k], v, raw);
+                lam = fmaf(t[k], v, lam);
+                gA = fmaf(Gn[k * FT + jj], t1[k], gA);
+                gC = fmaf(Gd[k * FT + jj], t1[k], gC);
+            }
+            const float il = 1.f / fmaxf(raw, kFloorPsd);
+            A = S * il * il;
+            cc = c * il;
+            gp = raw > kFloorPsd ? (-2.f * A * il * gA - cc * il * gC) : 0.f;
+            gs = gA * il * il;
+            ci = c / fmaxf(lam, kFloorPsd);
+        }
+        if (j < Jp) {
+            const size_t q = (((size_t)sm * N + n) * F + i) * (size_t)Jp + j;
+            g.glp[q] = gp;
+            g.gsa[q] = gs;
+        }
+        float* part = g.actp + ((((size_t)sm * N + n) * tiles + tile) * F + i) * (size_t)(2 * B);
+        for (int kb = 0; kb < B; kb += 8) {
+            float a[16];
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int k = kb + kk;
+                const float v = k < B ? Vt[k * FT + jj] : 0.f;
+                a[kk] = k < B ? fmaf(Gn[k * FT + jj], A, fmaf(Gd[k * FT + jj], cc, gp * v)) : 0.f;
+                a[8 + kk] = v * ci;
+            }
+            reduce_scatter<16>(a, lane);
+            if (!(lane & 1)) {
+                const int v = lane >> 1, k = kb + (v & 7);
+                if (k < B) part[v < 8 ? k : B + k] = a[0];
+            }
+        }
+    }
+}
+
+inline size_t act_smem(const Shape& s) { return sizeof(float) * (size_t)s.B * (3 * kEW * 32 + 2 * kEI); }
 
 // ---------------------------------------------------------------- D: gather dL/dV over bins
 constexpr int kID = 32;    // bins per block (blocks of one frame tile add into dL/dV)
@@ -508,13 +629,21 @@ cudaError_t grad_configure(const Shape& s)
 {
     GradBufs g;
     memset(&g, 0, sizeof(g));
+    const cudaError_t e = cudaFuncSetAttribute(grad_act_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)act_smem(s));
+    if (e != cudaSuccess) return e;
     return launch_bin(s, 1, nullptr, nullptr, g, nullptr, true);
+}
+
+size_t grad_act_partials(const Shape& s, int S)
+{
+    return (size_t)S * s.N * (size_t)((s.Jp + 31) / 32) * s.F * 2 * s.B;
 }
 
 cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, const StatePtrs* nxt,
                                    const GradBufs& g, int gin, bool first, cudaStream_t st, int* kernels)
 {
-    *kernels = 3;
+    *kernels = 4;
     if (first) {
         cudaError_t e = cudaMemsetAsync(g.e, 0, sizeof(double) * S * s.M, st);
         if (e != cudaSuccess) return e;
@@ -524,7 +653,7 @@ cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, 
             case 4: grad_norm_kernel<4><<<dim3(s.F, S), 256, 0, st>>>(s, nxt, g); break;
             default: return cudaErrorInvalidValue;
         }
-        *kernels = 4;
+        *kernels = 5;
     }
     cudaError_t e = cudaMemsetAsync(g.e_prev, 0, sizeof(double) * S * s.M, st);
     if (e != cudaSuccess) return e;
@@ -535,6 +664,8 @@ cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, 
         case 16: grad_vmu_kernel<16><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
         default: grad_vmu_kernel<32><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
     }
+    const dim3 egrid((s.Jp + kEW * 32 - 1) / (kEW * 32), (s.F + kEI - 1) / kEI, s.N * S);
+    grad_act_kernel<<<egrid, kEW * 32, act_smem(s), st>>>(s, cur, nxt, g);
     const dim3 fgrid((s.Jp + kGradTile - 1) / kGradTile, s.N, S);
     e = launch_bin(s, S, cur, nxt, g, st, false);
     if (e != cudaSuccess) return e;

@@ -38,6 +38,9 @@ struct GradBufs {
     float* glp;          // [S][N][F][Jp]  dL/d lambda' (lambda of T1 and V; 0 where floored)
     float* glt;          // [S][N][F][Jp]  dL/d lambda (of T and V; 0 where floored)
     float* aq;           // [S][N][F][Jp]  A = (delayed power) / lambda^2 of the basis MU
+    float* gsa;          // [S][N][F][Jp]  dL/d(delayed power) through the activation MU
+    float* actp;         // [S][N][ceil(Jp/32)][F][2B]  per 32-frame tile: sums of dL/dT1 and of
+                         //                the basis-MU denominator over its frames
     float* gnT;          // [S][N][FBp]    dL/d numT (basis MU numerator)
     float* gdT;          // [S][N][FBp]    dL/d denT
     double* e;           // [S][M]         normalisation sums of the iteration being reversed
@@ -48,6 +51,7 @@ struct GradBufs {
 };
 
 cudaError_t grad_configure(const Shape& s);
+size_t grad_act_partials(const Shape& s, int S);   // floats of GradBufs::actp
 // Enqueue the backward pass of one iteration (kernels A-D of grad.cu); gin selects the
 // gV buffer that holds dL/dV'; the other receives dL/dV. first: the first iteration reversed,
 // whose normalisation sums kernel A forms (later ones get them from the per-bin adjoint of the

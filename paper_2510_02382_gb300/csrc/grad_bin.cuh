@@ -75,15 +75,24 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     const size_t tb = (size_t)sm * N * FBp;
     const size_t fb = (size_t)sm * N;
 
-    // ---- bases of the bin, dL/dT1 = sigma_0^2 dL/dT', W_i, dL/dW1 = sigma dL/dW'
+    // ---- bases of the bin, dL/dT1 = sigma_0^2 dL/dT' plus the activation MU's part (the
+    // per-tile sums of kernel E), the basis-MU denominator, W_i, dL/dW1 = sigma dL/dW'
+    const int tiles = (Jp + 31) >> 5;
     for (int t = tid; t < N * B; t += NT) {
         const int n = t / B, k = t - n * B;
         const size_t o = (size_t)n * FBp + (size_t)i * B + k;
         const float s0 = sig[s.row0[n]];
+        const float* part = g.actp + ((((size_t)sm * N + n) * tiles) * F + i) * (size_t)(2 * B);
+        const size_t tstride = (size_t)F * 2 * B;
+        float ga = 0.f, dn = 0.f;
+        for (int q = 0; q < tiles; ++q) {
+            ga += part[q * tstride + k];
+            dn += part[q * tstride + B + k];
+        }
         Ti[t] = cur.T[o];
         T1i[t] = nxt.T[o] / (s0 * s0);
-        gT1[t] = g.gT[tb + o] * (s0 * s0);
-        denT[t] = 0.f;
+        gT1[t] = fmaf(g.gT[tb + o], s0 * s0, ga);
+        denT[t] = dn;
         gTacc[t] = 0.f;
     }
     if (tid < M * M) {
@@ -97,6 +106,10 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     {
         const float2* Yc = cur.Y + (size_t)i * M * Jp;
         for (int e = tid; e < M * Jp; e += NT) y0s[e] = Yc[e];
+        for (int e = tid; e < N * Jp; e += NT) {        // dL/dS through the activation MU (kernel E)
+            const int n = e / Jp, j = e - n * Jp;
+            gS[e] = g.gsa[((fb + n) * F + i) * (size_t)Jp + j];
+        }
         if (vstage)
             for (int e = tid; e < N * B * Jp / 4; e += NT)
                 reinterpret_cast<float4*>(Vst)[e] = reinterpret_cast<const float4*>(cur.V)[e];
@@ -236,66 +249,6 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         *S = acc;
         *c = (float)cnt;
     };
-
-    // ---- activation MU adjoint, this bin's part: numV = sum_i T1 A', denV = sum_i T1 c/lambda'
-    for (int n = 0; n < N; ++n) {
-        const float* Vn = Vsrc + (size_t)n * B * Jp;
-        const float* gnum = g.gnum + (fb + n) * (size_t)B * Jp;
-        const float* gden = g.gden + (fb + n) * (size_t)B * Jp;
-        float Ap[FPT], cp[FPT], gp[FPT], ci[FPT];
-#pragma unroll
-        for (int f = 0; f < FPT; ++f) {
-            const int j = tid + f * NT;
-            Ap[f] = cp[f] = gp[f] = ci[f] = 0.f;
-            if (j < J) {
-                float S, c;
-                delayed(n, j, &S, &c);
-                float raw = 0.f, gA = 0.f, gC = 0.f;
-                for (int k = 0; k < B; ++k) {
-                    const float t1 = T1i[n * B + k];
-                    raw = fmaf(t1, Vn[(size_t)k * Jp + j], raw);
-                    gA = fmaf(gnum[(size_t)k * Jp + j], t1, gA);
-                    gC = fmaf(gden[(size_t)k * Jp + j], t1, gC);
-                }
-                const float il = 1.f / fmaxf(raw, kFloorPsd);
-                const float A = S * il * il, cc = c * il;
-                Ap[f] = A;
-                cp[f] = cc;
-                gp[f] = raw > kFloorPsd ? (-2.f * A * il * gA - cc * il * gC) : 0.f;
-                gS[n * Jp + j] = gA * il * il;
-                ci[f] = c * invl[n * Jp + j];
-            }
-            if (j < Jp) g.glp[((fb + n) * F + i) * (size_t)Jp + j] = gp[f];
-        }
-        // per-bin sums over frames, 8 bases at a time: a[kk] -> dL/dT1, a[8 + kk] -> denT
-        for (int kb = 0; kb < B; kb += 8) {
-            float a[16];
-#pragma unroll
-            for (int v = 0; v < 16; ++v) a[v] = 0.f;
-#pragma unroll
-            for (int f = 0; f < FPT; ++f) {
-                const int j = tid + f * NT;
-                if (j < J) {
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const int k = kb + kk;
-                        if (k < B) {
-                            const size_t o = (size_t)k * Jp + j;
-                            const float vk = Vn[o];
-                            a[kk] += gnum[o] * Ap[f] + gden[o] * cp[f] + gp[f] * vk;
-                            a[8 + kk] = fmaf(vk, ci[f], a[8 + kk]);
-                        }
-                    }
-                }
-            }
-            reduce_scatter<16>(a, lane);
-            if (!(lane & 1)) {
-                const int v = lane >> 1, k = kb + (v & 7);
-                if (k < B) atomicAdd(v < 8 ? &gT1[n * B + k] : &denT[n * B + k], a[0]);
-            }
-        }
-    }
-    __syncthreads();
 
     // ---- basis MU adjoint (Eq. 17): T1 = T R, R = sqrt(numT / denT)
     for (int t = tid; t < N * B; t += NT) {
