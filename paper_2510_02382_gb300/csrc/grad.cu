@@ -155,11 +155,15 @@ __global__ void __launch_bounds__(kVT * kVG) grad_vmu_kernel(const Shape s, cons
 // lambda = T V). Block = kEW warps x 32 frames (one frame per lane) over kEI bins; V and the
 // two gradient planes of its frames are staged once in shared memory for all of its bins.
 // The per-bin sums go out per 32-frame tile (actp), added up by grad_bin_kernel.
+// REG (B <= 8): each lane keeps its frame's V and gradient-plane values in registers across
+// the bins, so a bin costs only the broadcast loads of its bases.
 constexpr int kEW = 8;     // warps (32-frame tiles) per block
 constexpr int kEI = 32;    // bins per block
 
-__global__ void __launch_bounds__(kEW * 32) grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab,
-                                                            const StatePtrs* __restrict__ nxt_tab, const GradBufs g)
+template <bool REG>
+__global__ void __launch_bounds__(kEW * 32, REG ? 4 : 1)
+grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const StatePtrs* __restrict__ nxt_tab,
+                const GradBufs g)
 {
     extern __shared__ float esm[];
     constexpr int FT = kEW * 32;                       // frames per block
@@ -209,6 +213,15 @@ __global__ void __launch_bounds__(kEW * 32) grad_act_kernel(const Shape s, const
         isg[l] = sg > 0.f ? 1.f / (sg * sg) : 0.f;
     }
     const int tiles = (Jp + 31) >> 5, tile = (j0 >> 5) + w;
+    float vr[8], gnr[8], gdr[8];                       // REG: this frame's V, dL/dnumV, dL/ddenV
+    if constexpr (REG) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            vr[k] = k < B ? Vt[k * FT + jj] : 0.f;
+            gnr[k] = k < B ? Gn[k * FT + jj] : 0.f;
+            gdr[k] = k < B ? Gd[k * FT + jj] : 0.f;
+        }
+    }
     for (int ii = 0; ii < ic; ++ii) {
         const int i = i0 + ii;
         float A = 0.f, cc = 0.f, gp = 0.f, gs = 0.f, ci = 0.f;
@@ -221,13 +234,24 @@ __global__ void __launch_bounds__(kEW * 32) grad_act_kernel(const Shape s, const
             const float* t1 = T1s + ii * B;
             const float* t = Ts + ii * B;
             float raw = 0.f, gA = 0.f, gC = 0.f, lam = 0.f;
+            if constexpr (REG) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float tk1 = k < B ? t1[k] : 0.f, tk = k < B ? t[k] : 0.f;
+                    raw = fmaf(tk1, vr[k], raw);
+                    lam = fmaf(tk, vr[k], lam);
+                    gA = fmaf(gnr[k], tk1, gA);
+                    gC = fmaf(gdr[k], tk1, gC);
+                }
+            } else {
 #pragma unroll 4
-            for (int k = 0; k < B; ++k) {
-                const float v = Vt[k * FT + jj];
-                raw = fmaf(t1[k], v, raw);
-                lam = fmaf(t[k], v, lam);
-                gA = fmaf(Gn[k * FT + jj], t1[k], gA);
-                gC = fmaf(Gd[k * FT + jj], t1[k], gC);
+                for (int k = 0; k < B; ++k) {
+                    const float v = Vt[k * FT + jj];
+                    raw = fmaf(t1[k], v, raw);
+                    lam = fmaf(t[k], v, lam);
+                    gA = fmaf(Gn[k * FT + jj], t1[k], gA);
+                    gC = fmaf(Gd[k * FT + jj], t1[k], gC);
+                }
             }
             const float il = 1.f / fmaxf(raw, kFloorPsd);
             A = S * il * il;
@@ -247,9 +271,14 @@ __global__ void __launch_bounds__(kEW * 32) grad_act_kernel(const Shape s, const
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 const int k = kb + kk;
-                const float v = k < B ? Vt[k * FT + jj] : 0.f;
-                a[kk] = k < B ? fmaf(Gn[k * FT + jj], A, fmaf(Gd[k * FT + jj], cc, gp * v)) : 0.f;
-                a[8 + kk] = v * ci;
+                if constexpr (REG) {
+                    a[kk] = fmaf(gnr[kk], A, fmaf(gdr[kk], cc, gp * vr[kk]));
+                    a[8 + kk] = vr[kk] * ci;
+                } else {
+                    const float v = k < B ? Vt[k * FT + jj] : 0.f;
+                    a[kk] = k < B ? fmaf(Gn[k * FT + jj], A, fmaf(Gd[k * FT + jj], cc, gp * v)) : 0.f;
+                    a[8 + kk] = v * ci;
+                }
             }
             reduce_scatter<16>(a, lane);
             if (!(lane & 1)) {
@@ -629,8 +658,10 @@ cudaError_t grad_configure(const Shape& s)
 {
     GradBufs g;
     memset(&g, 0, sizeof(g));
-    const cudaError_t e = cudaFuncSetAttribute(grad_act_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)act_smem(s));
+    const cudaError_t e = s.B <= 8 ? cudaFuncSetAttribute(grad_act_kernel<true>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)act_smem(s))
+                                   : cudaFuncSetAttribute(grad_act_kernel<false>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)act_smem(s));
     if (e != cudaSuccess) return e;
     return launch_bin(s, 1, nullptr, nullptr, g, nullptr, true);
 }
@@ -665,7 +696,8 @@ cudaError_t grad_enqueue_iteration(const Shape& s, int S, const StatePtrs* cur, 
         default: grad_vmu_kernel<32><<<vgrid, kVT * kVG, 0, st>>>(s, cur, nxt, g, gin); break;
     }
     const dim3 egrid((s.Jp + kEW * 32 - 1) / (kEW * 32), (s.F + kEI - 1) / kEI, s.N * S);
-    grad_act_kernel<<<egrid, kEW * 32, act_smem(s), st>>>(s, cur, nxt, g);
+    if (s.B <= 8) grad_act_kernel<true><<<egrid, kEW * 32, act_smem(s), st>>>(s, cur, nxt, g);
+    else grad_act_kernel<false><<<egrid, kEW * 32, act_smem(s), st>>>(s, cur, nxt, g);
     const dim3 fgrid((s.Jp + kGradTile - 1) / kGradTile, s.N, S);
     e = launch_bin(s, S, cur, nxt, g, st, false);
     if (e != cudaSuccess) return e;
