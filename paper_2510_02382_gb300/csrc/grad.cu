@@ -168,6 +168,7 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     extern __shared__ float esm[];
     constexpr int FT = kEW * 32;                       // frames per block
     const int N = s.N, B = s.B, F = s.F, J = s.J, Jp = s.Jp, FBp = s.FBp, M = s.M;
+    const int TB = REG ? 8 : B;                        // stride of the staged bases (REG: zero-padded to 8)
     const int sm = blockIdx.z / N, n = blockIdx.z - sm * N;
     const int j0 = blockIdx.x * FT, i0 = blockIdx.y * kEI;
     const int ic = min(kEI, F - i0);
@@ -175,8 +176,8 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     float* Vt = esm;                                   // [B][FT]
     float* Gn = Vt + B * FT;                           // [B][FT]
     float* Gd = Gn + B * FT;                           // [B][FT]
-    float* T1s = Gd + B * FT;                          // [kEI][B]
-    float* Ts = T1s + kEI * B;                         // [kEI][B]
+    float* T1s = Gd + B * FT;                          // [kEI][TB]
+    float* Ts = T1s + kEI * TB;                        // [kEI][TB]
     const StatePtrs cur = cur_tab[sm], nxt = nxt_tab[sm];
     const float* sig = g.sig + sm * M;
     const int r0 = s.row0[n], Lq = s.Ln[n];
@@ -196,10 +197,11 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         Gn[e] = gn;
         Gd[e] = gd;
     }
-    for (int e = tid; e < ic * B; e += blockDim.x) {
-        const size_t o = (size_t)n * FBp + (size_t)i0 * B + e;       // bins i0.. are contiguous
-        T1s[e] = nxt.T[o] * inv;
-        Ts[e] = cur.T[o];
+    for (int e = tid; e < ic * TB; e += blockDim.x) {
+        const int ii = e / TB, k = e - ii * TB;
+        const size_t o = (size_t)n * FBp + (size_t)(i0 + ii) * B + k;
+        T1s[e] = k < B ? nxt.T[o] * inv : 0.f;
+        Ts[e] = k < B ? cur.T[o] : 0.f;
     }
     __syncthreads();
     if (j0 + w * 32 >= Jp) return;                     // a warp past the last frame tile
@@ -213,6 +215,12 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         isg[l] = sg > 0.f ? 1.f / (sg * sg) : 0.f;
     }
     const int tiles = (Jp + 31) >> 5, tile = (j0 >> 5) + w;
+    // per-bin pointers, advanced bin by bin: the rows (n, 0..) at this frame, the two output
+    // planes at this frame, the tile's partial sums
+    const float2* Yr = nxt.Y + ((size_t)i0 * M + r0) * Jp + (live ? j : 0);
+    const size_t ystep = (size_t)M * Jp;
+    const size_t q0 = (((size_t)sm * N + n) * F + i0) * (size_t)Jp + j;
+    float* part = g.actp + ((((size_t)sm * N + n) * tiles + tile) * F + i0) * (size_t)(2 * B);
     float vr[8], gnr[8], gdr[8];                       // REG: this frame's V, dL/dnumV, dL/ddenV
     if constexpr (REG) {
 #pragma unroll
@@ -222,28 +230,30 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
             gdr[k] = k < B ? Gd[k * FT + jj] : 0.f;
         }
     }
-    for (int ii = 0; ii < ic; ++ii) {
-        const int i = i0 + ii;
+    for (int ii = 0; ii < ic; ++ii, Yr += ystep, part += 2 * B) {
         float A = 0.f, cc = 0.f, gp = 0.f, gs = 0.f, ci = 0.f;
         if (live) {
-            const float2* Yb = nxt.Y + (size_t)i * M * Jp;
             float S = 0.f;
 #pragma unroll
             for (int l = 0; l < kGradMaxM; ++l)
-                if (l < Lq && j + l < J) S = fmaf(abs2(Yb[(size_t)(r0 + l) * Jp + j + l]), isg[l], S);
-            const float* t1 = T1s + ii * B;
-            const float* t = Ts + ii * B;
+                if (l < Lq && j + l < J) S = fmaf(abs2(Yr[(size_t)l * (Jp + 1)]), isg[l], S);
             float raw = 0.f, gA = 0.f, gC = 0.f, lam = 0.f;
             if constexpr (REG) {
+                const float4* t1 = reinterpret_cast<const float4*>(T1s + ii * 8);
+                const float4* t = reinterpret_cast<const float4*>(Ts + ii * 8);
+                const float4 a1 = t1[0], b1 = t1[1], a0 = t[0], b0 = t[1];
+                const float tk1[8] = {a1.x, a1.y, a1.z, a1.w, b1.x, b1.y, b1.z, b1.w};
+                const float tk[8] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const float tk1 = k < B ? t1[k] : 0.f, tk = k < B ? t[k] : 0.f;
-                    raw = fmaf(tk1, vr[k], raw);
-                    lam = fmaf(tk, vr[k], lam);
-                    gA = fmaf(gnr[k], tk1, gA);
-                    gC = fmaf(gdr[k], tk1, gC);
+                    raw = fmaf(tk1[k], vr[k], raw);
+                    lam = fmaf(tk[k], vr[k], lam);
+                    gA = fmaf(gnr[k], tk1[k], gA);
+                    gC = fmaf(gdr[k], tk1[k], gC);
                 }
             } else {
+                const float* t1 = T1s + ii * TB;
+                const float* t = Ts + ii * TB;
 #pragma unroll 4
                 for (int k = 0; k < B; ++k) {
                     const float v = Vt[k * FT + jj];
@@ -253,19 +263,18 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
                     gC = fmaf(Gd[k * FT + jj], t1[k], gC);
                 }
             }
-            const float il = 1.f / fmaxf(raw, kFloorPsd);
+            const float il = __frcp_rn(fmaxf(raw, kFloorPsd));
             A = S * il * il;
             cc = c * il;
             gp = raw > kFloorPsd ? (-2.f * A * il * gA - cc * il * gC) : 0.f;
             gs = gA * il * il;
-            ci = c / fmaxf(lam, kFloorPsd);
+            ci = c * __frcp_rn(fmaxf(lam, kFloorPsd));
         }
         if (j < Jp) {
-            const size_t q = (((size_t)sm * N + n) * F + i) * (size_t)Jp + j;
+            const size_t q = q0 + (size_t)ii * Jp;
             g.glp[q] = gp;
             g.gsa[q] = gs;
         }
-        float* part = g.actp + ((((size_t)sm * N + n) * tiles + tile) * F + i) * (size_t)(2 * B);
         for (int kb = 0; kb < B; kb += 8) {
             float a[16];
 #pragma unroll
@@ -289,7 +298,11 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     }
 }
 
-inline size_t act_smem(const Shape& s) { return sizeof(float) * (size_t)s.B * (3 * kEW * 32 + 2 * kEI); }
+inline size_t act_smem(const Shape& s)
+{
+    const int tb = s.B <= 8 ? 8 : s.B;                 // the staged bases' stride (see TB)
+    return sizeof(float) * ((size_t)s.B * 3 * kEW * 32 + (size_t)2 * kEI * tb);
+}
 
 // ---------------------------------------------------------------- D: gather dL/dV over bins
 constexpr int kID = 32;    // bins per block (blocks of one frame tile add into dL/dV)
