@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(kVT * kVG) grad_vmu_kernel(const Shape s, cons
 // delayed power S of |Y1|^2 = |Y'|^2 / sigma^2 over the source's taps, c the tap count and
 // lambda' = T1 V: A = S / lambda'^2, dL/dlambda' = -2 A gA / lambda' - c gC / lambda'^2
 // (0 where lambda' is floored) with gA = sum_k dL/dnumV T1, gC = sum_k dL/ddenV T1, and
-// dL/dS = gA / lambda'^2; per bin the sums over frames of dL/dT1 (sum_j dL/dnumV A +
+// dL/dS = gA / lambda'^2, and 1/lambda of the iteration (lambda = T V, floored; 0 past J) for the
+// per-bin kernel; per bin the sums over frames of dL/dT1 (sum_j dL/dnumV A +
 // dL/ddenV c/lambda' + dL/dlambda' V) and of the basis-MU denominator (sum_j V c/lambda with
 // lambda = T V). Block = kEW warps x 32 frames (one frame per lane) over kEI bins; V and the
 // two gradient planes of its frames are staged once in shared memory for all of its bins.
@@ -231,7 +232,7 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         }
     }
     for (int ii = 0; ii < ic; ++ii, Yr += ystep, part += 2 * B) {
-        float A = 0.f, cc = 0.f, gp = 0.f, gs = 0.f, ci = 0.f;
+        float A = 0.f, cc = 0.f, gp = 0.f, gs = 0.f, ci = 0.f, ilam = 0.f;
         if (live) {
             float S = 0.f;
 #pragma unroll
@@ -268,12 +269,14 @@ grad_act_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
             cc = c * il;
             gp = raw > kFloorPsd ? (-2.f * A * il * gA - cc * il * gC) : 0.f;
             gs = gA * il * il;
-            ci = c * __frcp_rn(fmaxf(lam, kFloorPsd));
+            ilam = __frcp_rn(fmaxf(lam, kFloorPsd));
+            ci = c * ilam;
         }
         if (j < Jp) {
             const size_t q = q0 + (size_t)ii * Jp;
             g.glp[q] = gp;
             g.gsa[q] = gs;
+            g.ilp[q] = ilam;
         }
         for (int kb = 0; kb < B; kb += 8) {
             float a[16];

@@ -39,6 +39,7 @@ struct GradBufs {
     float* glt;          // [S][N][F][Jp]  dL/d lambda (of T and V; 0 where floored)
     float* aq;           // [S][N][F][Jp]  A = (delayed power) / lambda^2 of the basis MU
     float* gsa;          // [S][N][F][Jp]  dL/d(delayed power) through the activation MU
+    float* ilp;          // [S][N][F][Jp]  1/lambda of the iteration's T and V (0 past J)
     float* actp;         // [S][N][ceil(Jp/32)][F][2B]  per 32-frame tile: sums of dL/dT1 and of
                          //                the basis-MU denominator over its frames
     float* gnT;          // [S][N][FBp]    dL/d numT (basis MU numerator)

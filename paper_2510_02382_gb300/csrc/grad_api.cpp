@@ -262,7 +262,7 @@ int ctfmnmf_grad_create(const ctfmnmf_dims* dims, const int* Ln, int batch, int 
               dalloc(g, &gb.gY, nY) && dalloc(g, &gb.gW, (size_t)S * F * M * M) && dalloc(g, &gb.gT, nT) &&
               dalloc(g, &gb.gV[0], nV) && dalloc(g, &gb.gV[1], nV) && dalloc(g, &gb.gnum, nV) &&
               dalloc(g, &gb.gden, nV) && dalloc(g, &gb.glp, nL) && dalloc(g, &gb.glt, nL) &&
-              dalloc(g, &gb.aq, nL) && dalloc(g, &gb.gsa, nL) && dalloc(g, &gb.actp, ctf::grad_act_partials(s, S)) &&
+              dalloc(g, &gb.aq, nL) && dalloc(g, &gb.gsa, nL) && dalloc(g, &gb.ilp, nL) && dalloc(g, &gb.actp, ctf::grad_act_partials(s, S)) &&
               dalloc(g, &gb.gnT, nT) && dalloc(g, &gb.gdT, nT) &&
               dalloc(g, &gb.e, (size_t)S * M) && dalloc(g, &gb.e_prev, (size_t)S * M);
     if (!ok) {

@@ -101,14 +101,17 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
         const float2 gw = g.gW[(((size_t)sm * F + i) * M + p) * M + c];
         gWs[p][c] = make_float2(gw.x * sig[p], gw.y * sig[p]);
     }
-    // ---- the rows at the start of the iteration; V (when staged); then 1/lambda of the
-    // iteration's T, V from the staged copy
+    // ---- the rows at the start of the iteration; V (when staged); 1/lambda of the iteration's
+    // T, V and dL/dS through the activation MU (both from kernel E; [N][F][Jp] planes, so a
+    // bin's N rows are Jp apart only within one source)
     {
         const float2* Yc = cur.Y + (size_t)i * M * Jp;
         for (int e = tid; e < M * Jp; e += NT) y0s[e] = Yc[e];
-        for (int e = tid; e < N * Jp; e += NT) {        // dL/dS through the activation MU (kernel E)
+        for (int e = tid; e < N * Jp; e += NT) {
             const int n = e / Jp, j = e - n * Jp;
-            gS[e] = g.gsa[((fb + n) * F + i) * (size_t)Jp + j];
+            const size_t q = ((fb + n) * F + i) * (size_t)Jp + j;
+            gS[e] = g.gsa[q];
+            invl[e] = g.ilp[q];
         }
         if (vstage)
             for (int e = tid; e < N * B * Jp / 4; e += NT)
@@ -116,17 +119,6 @@ grad_bin_kernel(const Shape s, const StatePtrs* __restrict__ cur_tab, const Stat
     }
     __syncthreads();
     const float* Vsrc = vstage ? Vst : cur.V;              // V [N][B][Jp], shared or global
-    for (int e = tid; e < N * Jp; e += NT) {
-        const int n = e / Jp, j = e - n * Jp;
-        float v = 0.f;
-        if (j < J) {
-            float lam = 0.f;
-            for (int k = 0; k < B; ++k) lam = fmaf(Ti[n * B + k], Vsrc[((size_t)n * B + k) * Jp + j], lam);
-            v = 1.f / fmaxf(lam, kFloorPsd);
-        }
-        invl[e] = v;
-    }
-    __syncthreads();
     const float thr = 1.f / kFloorPsd;                     // 1/lambda at (or past) the floor
 
     auto phi = [&](int p, int j) -> float {   // 1/lambda_{n(p), j - l(p)}, 0 when masked
