@@ -549,8 +549,9 @@ __global__ void grad_copy_kernel(const Shape s, const StatePtrs* __restrict__ sr
 // As finalize_kernel (the pending normalisation applied to Y, W, log|det|, T, 1/lambda) for every
 // mixture of the batch; also records sigma_r = the applied scale. One block per (bin, mixture)
 // covering all of its rows with 16-byte accesses (two complex values, four 1/lambda). With a
-// snapshot table (snap != NULL) the normalised Y, W, T and a copy of V also go to snap[mixture]:
-// the state at the start of the next iteration, kept for the backward pass.
+// snapshot table (snap != NULL) the normalised Y, W, T and a copy of V go to snap[mixture]
+// instead (the state at the start of the next iteration, kept for the backward pass) and the
+// live state keeps its pending normalisation, which the next bin phase applies as it loads.
 __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* __restrict__ sig,
                                      const StatePtrs* __restrict__ snap)
 {
@@ -570,15 +571,28 @@ __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* _
         const float c = sc[e / R4];
         const float4 v = Yb[e];
         const float4 o = make_float4(v.x * c, v.y * c, v.z * c, v.w * c);
-        Yb[e] = o;
         if (Ys) Ys[e] = o;
+        else Yb[e] = o;
     }
     if ((int)threadIdx.x < M * M) {
         float2* w = d.W + (size_t)i * M * M + threadIdx.x;
         const float c = sc[threadIdx.x / M];
         const float2 o = make_float2(w->x * c, w->y * c);
-        *w = o;
         if (snap) sp.W[(size_t)i * M * M + threadIdx.x] = o;
+        else *w = o;
+    }
+    if (snap) {
+        for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
+            const int n = t / B, k = t - n * B;
+            const float c = sc[s.row0[n]];
+            const size_t o = (size_t)n * s.FBp + (size_t)i * B + k;
+            sp.T[o] = d.T[o] * (c * c);
+        }
+        const size_t nV4 = (size_t)N * B * Jp / 4;     // V [N][B][Jp], split over the bins
+        for (size_t e = (size_t)i * blockDim.x + threadIdx.x; e < nV4; e += (size_t)s.F * blockDim.x)
+            reinterpret_cast<float4*>(sp.V)[e] = reinterpret_cast<const float4*>(d.V)[e];
+        if (i == 0 && (int)threadIdx.x < M) sig[sm * M + threadIdx.x] = sc[threadIdx.x];
+        return;
     }
     if (threadIdx.x == 0) {
         double f = d.ldm[i];
@@ -590,15 +604,7 @@ __global__ void grad_finalize_kernel(const MixDesc* __restrict__ mixes, float* _
     for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
         const int n = t / B, k = t - n * B;
         const float c = sc[s.row0[n]];
-        const size_t o = (size_t)n * s.FBp + (size_t)i * B + k;
-        const float v = d.T[o] * (c * c);
-        d.T[o] = v;
-        if (snap) sp.T[o] = v;
-    }
-    if (snap) {                                          // V [N][B][Jp], split over the bins
-        const size_t nV4 = (size_t)N * B * Jp / 4;
-        for (size_t e = (size_t)i * blockDim.x + threadIdx.x; e < nV4; e += (size_t)s.F * blockDim.x)
-            reinterpret_cast<float4*>(sp.V)[e] = reinterpret_cast<const float4*>(d.V)[e];
+        d.T[(size_t)n * s.FBp + (size_t)i * B + k] *= c * c;
     }
     const int L4 = Jp >> 2;                              // float4 per row of 1/lambda
     float4* il = reinterpret_cast<float4*>(d.invlam + (size_t)i * N * Jp);
@@ -757,7 +763,7 @@ cudaError_t grad_launch_finalize(const Shape& s, int S, const MixDesc* mixes, fl
                                  const StatePtrs* snap)
 {
     grad_finalize_kernel<<<dim3(s.F, S), 256, 0, st>>>(mixes, sig, snap);
-    grad_reset_scale_kernel<<<S, 32, 0, st>>>(mixes);
+    if (!snap) grad_reset_scale_kernel<<<S, 32, 0, st>>>(mixes);   // with a snapshot the scale stays pending
     return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ long long record_segment_direct(ctfmnmf_grad* g, int len, cudaStream_t st)
         if (ctf::batch_enqueue(g->batch, 1, st) != cudaSuccess ||
             ctf::grad_launch_finalize(s, S, g->mix, g->sig + (size_t)t * S * s.M, st, snap) != cudaSuccess)
             return -1;
-        n += 2;
+        n += snap ? 1 : 2;                              // finalize (+ scale reset after the last)
     }
     int info[5] = {0, 0, 0, 0, 0};
     ctfmnmf_batch_info(g->batch, info);
