@@ -33,7 +33,7 @@ void free_state(ctfmnmf* h)
 {
     State& d = h->d;
     void* ptrs[] = {d.Y, d.W, d.logdet, d.T, d.V, d.invlam, d.P, d.mupart, d.scale, d.flag,
-                    d.cost_part, d.cost_out, d.staging, d.ldm, d.lde, d.sync, d.X};
+                    d.cost_part, d.cost_out, d.staging, d.detb, d.ldm, d.lde, d.sync, d.X};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     memset(&h->d, 0, sizeof(h->d));
@@ -315,6 +315,7 @@ int ctfmnmf_create_ex(const ctfmnmf_dims* dims, const int* Ln, const ctfmnmf_opt
         {(void**)&d.flag, sizeof(int) * 4},
         {(void**)&d.cost_part, sizeof(double) * F},
         {(void**)&d.cost_out, sizeof(double)},
+        {(void**)&d.detb, sizeof(float) * F},
         {(void**)&d.ldm, sizeof(double) * F},
         {(void**)&d.lde, sizeof(int) * F},
         {(void**)&d.sync, sizeof(unsigned) * 32},

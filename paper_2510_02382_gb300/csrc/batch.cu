@@ -54,7 +54,7 @@ batch_frame_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ w
     }
 #endif
     if (w.y < 0) {
-        scales_fp64(s, d, normalize, reinterpret_cast<double*>(fsm4));
+        scales_fp64<true>(s, d, normalize, reinterpret_cast<double*>(fsm4));
         return;
     }
     const Grp g{(int)threadIdx.x, kBatchFrameThreads, 0};

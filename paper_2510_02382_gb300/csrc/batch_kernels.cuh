@@ -41,12 +41,7 @@ batch_bin_kernel(const MixDesc* __restrict__ mixes, const int2* __restrict__ wor
     __syncthreads();
     apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
     const float detf = bin_body<M, FPT, true, KB, false, false, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
-    if (g.tid == 0) {
-        double f = (double)detf;
-#pragma unroll
-        for (int r = 0; r < M; ++r) f *= (double)s_scale[r];
-        logdet_mul(d, i, f);
-    }
+    if (g.tid == 0) d.detb[i] = det_factor<M>(detf, s_scale);   // folded by the frame phase
 }
 
 template <int M, int FPT, int KB>

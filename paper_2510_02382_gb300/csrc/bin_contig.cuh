@@ -408,12 +408,7 @@ __device__ __forceinline__ void contig_bin_body(const Shape& s, const State& d, 
         for (int w = 0; w < NW; ++w) t += (double)rps[w * 8 + tid];
         __stcg(d.mupart + (size_t)i * M + tid, t);
     }
-    if (tid == 0) {
-        double f = (double)detf;
-#pragma unroll
-        for (int r = 0; r < M; ++r) f *= (double)sc[r];
-        logdet_mul(d, i, f);
-    }
+    if (tid == 0) d.detb[i] = det_factor<M>(detf, sc);   // folded by the frame phase
 }
 
 // Two-kernel path: one block per bin.

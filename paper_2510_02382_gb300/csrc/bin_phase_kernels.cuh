@@ -31,12 +31,7 @@ bin_phase_kernel(const Shape s, const State d, const int v_tap0)
     __syncthreads();
     apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
     const float detf = bin_body<M, FPT, true, KB, false, true, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
-    if (g.tid == 0) {
-        double f = (double)detf;
-#pragma unroll
-        for (int r = 0; r < M; ++r) f *= (double)s_scale[r];
-        logdet_mul(d, i, f);
-    }
+    if (g.tid == 0) d.detb[i] = det_factor<M>(detf, s_scale);   // folded by the frame phase
 }
 
 // IP update (Eqs. 9-10) in place of the ISS sweep: same tail (rows, P, basis MU).
@@ -58,12 +53,7 @@ ip_bin_kernel(const Shape s, const State d, const int v_tap0)
     __syncthreads();
     apply_bin_scale<M, FPT>(g, s_scale, y, wcol);
     const float detf = bin_body<M, FPT, true, 16, true, false, true>(s, d, i, g, smem, y, wcol, Yb, Wb, s_scale, v_tap0);
-    if (g.tid == 0) {
-        double f = (double)detf;
-#pragma unroll
-        for (int r = 0; r < M; ++r) f *= (double)s_scale[r];
-        logdet_mul(d, i, f);
-    }
+    if (g.tid == 0) d.detb[i] = det_factor<M>(detf, s_scale);   // folded by the frame phase
 }
 
 template <int M, int FPT, int KB>

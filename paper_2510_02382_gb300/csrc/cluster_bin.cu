@@ -302,12 +302,7 @@ cluster_bin_kernel(const Shape s, const State d, const int v_tap0, const int Jc)
 #pragma unroll
             for (int p = 0; p < M; ++p) __stcg(d.W + ((size_t)i * M + p) * M + tid, wcol[p]);
         }
-        if (tid == 0) {
-            double f = (double)detf;
-#pragma unroll
-            for (int r = 0; r < M; ++r) f *= (double)s_scale[r];
-            logdet_mul(d, i, f);
-        }
+        if (tid == 0) d.detb[i] = det_factor<M>(detf, s_scale);   // folded by the frame phase
     }
     cl.sync();                                      // no block leaves while its shared memory is read
 }

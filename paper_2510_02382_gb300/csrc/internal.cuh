@@ -53,6 +53,8 @@ struct State {
     float* P;
     double* mupart;
     float* scale;
+    float* detb;        // [F] the bin phase's |det W_i| factor of this iteration (pending scale
+                        //     included), folded into ldm/lde by the frame phase
     double* ldm;        // [F] mantissa of the log-det product not yet folded into logdet
     int* lde;           // [F] its binary exponent
     unsigned* sync;     // grid barrier words: [0] abort, [1] arrivals, [2] generation

@@ -165,11 +165,14 @@ cudaError_t launch_psd(const Shape& s, const State& d, cudaStream_t st)
 }
 
 // ------------------------------------------------------------------ frame phase
-// Two-kernel path: block 0 forms the normalisation scale of this iteration from the per-bin
-// row powers (FP64, Eq. 19) and stores it as the pending scale of the next bin phase; every
-// other block (256 threads) takes one (8-frame tile, source) item, whose device code is
+// Two-kernel path: blocks 0 .. kFoldBlocks-1 fold the bin phase's |det| factors into the FP64
+// log-det pairs, one bin per thread (FP64 is slow on this GPU, so no single block takes all
+// bins); block 0 also forms the normalisation scale of this iteration from the per-bin row
+// powers (FP64, Eq. 19) and stores it as the pending scale of the next bin phase; every other
+// block (256 threads) takes one (8-frame tile, source) item, whose device code is
 // frame_item() in phases.cuh (the items need no scale: the next bin phase applies it).
 constexpr int kFrameThreads = 256;
+constexpr int kFoldBlocks = 8;
 constexpr int kFrameSmemBytes = 48 * 1024;
 
 // EXACT: s.B equals the class width BB (the per-basis bounds tests fold away).
@@ -180,20 +183,22 @@ __global__ void __launch_bounds__(kFrameThreads) frame_phase_kernel(const Shape 
 {
     extern __shared__ float4 fsm4[];
 #ifdef CTFMNMF_DEBUG
-    if ((int)blockIdx.x > (s.Jp / kFrameTile) * s.N) {     // an item outside the shape
+    if ((int)blockIdx.x >= (s.Jp / kFrameTile) * s.N + kFoldBlocks) {     // an item outside the shape
         if (threadIdx.x == 0) atomicOr(d.flag + 3, 1);
         return;
     }
 #endif
-    if (blockIdx.x == 0) {
-        scales_fp64(s, d, normalize, reinterpret_cast<double*>(fsm4));
+    if (blockIdx.x < kFoldBlocks) {
+        fold_logdet(s, d, blockIdx.x * kFrameThreads + threadIdx.x, kFoldBlocks * kFrameThreads);
+        if (blockIdx.x == 0) scales_fp64<false>(s, d, normalize, reinterpret_cast<double*>(fsm4));
         return;
     }
     const Grp g{(int)threadIdx.x, kFrameThreads, 0};
+    const int item = blockIdx.x - kFoldBlocks;
     if constexpr (BB <= 16)
-        frame_item<BB, EXACT, true>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
+        frame_item<BB, EXACT, true>(s, d, item, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
     else
-        frame_item_wide<BB, EXACT, true>(s, d, blockIdx.x - 1, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
+        frame_item_wide<BB, EXACT, true>(s, d, item, g, reinterpret_cast<float*>(fsm4), FC, v_tap0);
 }
 
 static int frame_fc(const Shape& s, int BB)
@@ -239,7 +244,7 @@ static void frame_launch(const Shape& s, const State& d, int v_tap0, int normali
 cudaError_t launch_frame_phase(const Shape& s, const State& d, int v_tap0, int normalize,
                                cudaStream_t st)
 {
-    const int items = (s.Jp / kFrameTile) * s.N + 1;       // + block 0, the scale
+    const int items = (s.Jp / kFrameTile) * s.N + kFoldBlocks;   // + the fold and scale blocks
     const int BB = frame_bb(s.B);
     const int FC = frame_fc(s, BB);
     if (FC < 4 || (FC * s.B) % 4 != 0 || s.Jp % kFrameTile != 0) return cudaErrorInvalidValue;

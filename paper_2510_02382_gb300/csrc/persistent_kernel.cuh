@@ -155,7 +155,7 @@ persistent_kernel(const Shape s, const State d, const PersistArgs pa)
             else frame_item_wide<BB>(s, d, item, cta, psm, pa.fc, pa.v_tap0);
         }
         if (blockIdx.x == gridDim.x - 1) {
-            scales_fp64(s, d, pa.normalize, red_cta);
+            scales_fp64<false>(s, d, pa.normalize, red_cta);
             __syncthreads();
         }
         alive = grid_sync(d, 2u * it + 2u, pa.timeout_ns, false);

@@ -680,6 +680,25 @@ __host__ __device__ inline int frame_chunk(int avail_floats, int B, int fixed)
 // thread r < M stores it to d.scale[r]. Run once per iteration and mixture, by a block of
 // its own, so that its FP64 work (slow on this GPU) is off every other block's path.
 // red_cta: shared scratch of (blockDim.x / 32) * CTFMNMF_MAX_M doubles.
+// The |det W_i| factor of one bin phase: the ISS normalisers' product detf times the pending
+// scale that phase applied to the rows, an FP32 product (detf is one already); the frame
+// phase folds it into the FP64 log-det pair (fold_logdet), so no bin block ends on FP64 work.
+template <int M>
+__device__ __forceinline__ float det_factor(float detf, const float* sc)
+{
+#pragma unroll
+    for (int r = 0; r < M; ++r) detf *= sc[r];
+    return detf;
+}
+
+// Bins i = first, first + stride, ... of this iteration's factors into the log-det pair.
+__device__ __forceinline__ void fold_logdet(const Shape& s, const State& d, int first, int stride)
+{
+    for (int i = first; i < s.F; i += stride) logdet_mul(d, i, (double)__ldcg(d.detb + i));
+}
+
+// FOLD: this block also folds every bin's factor (one block per mixture: the batched form).
+template <bool FOLD>
 __device__ __forceinline__ void scales_fp64(const Shape& s, const State& d, int normalize, double* red_cta)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -705,6 +724,7 @@ __device__ __forceinline__ void scales_fp64(const Shape& s, const State& d, int 
         const double ms = t / ((double)F * (double)s.J);
         d.scale[tid] = (normalize && ms > 0.0) ? (float)rsqrt(ms) : 1.0f;
     }
+    if constexpr (FOLD) fold_logdet(s, d, tid, blockDim.x);
 }
 
 // Copy `count` contiguous floats of bases (16-byte aligned source; count rounded up to a
