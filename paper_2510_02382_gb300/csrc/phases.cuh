@@ -573,10 +573,13 @@ __device__ __forceinline__ float bin_body(const Shape& s, const State& d, const 
         const float tn = (den > 0.f) ? tcur * sqrtf(num / den) : tcur;
         __stcg(Tp, fmaxf(tn, s.floor_nmf));
     }
-    if (g.tid < M) {                                  // the bin's row power in FP64 (Eq. 19)
+    // the bin's row power in FP64 (Eq. 19), by warp 1 where there is one, beside warp 0's
+    // basis update above
+    const int mt = g.tid - (NW > 1 ? 32 : 0);
+    if (mt >= 0 && mt < M) {
         double t = 0.0;
-        for (int w = 0; w < NW; ++w) t += (double)red[w * 8 + g.tid];
-        __stcg(d.mupart + (size_t)i * M + g.tid, t);
+        for (int w = 0; w < NW; ++w) t += (double)red[w * 8 + mt];
+        __stcg(d.mupart + (size_t)i * M + mt, t);
     }
     if constexpr (!ONE) grp_sync(g);     // shared memory is reused by the next item of this group
     return detf;
