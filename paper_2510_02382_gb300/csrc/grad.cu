@@ -14,8 +14,8 @@
 //                                                  per-tile sums of dL/dT1 and the basis-MU
 //                                                  denominator)
 //   C grad_bin_kernel      (bin, mixture)          recompute the ISS sweep; adjoint of the
-//                                                  normalisation, the activation MU (per-bin
-//                                                  parts), the basis MU and the ISS sweep;
+//                                                  normalisation, the basis MU (with kernel E's
+//                                                  activation-MU parts) and the ISS sweep;
 //                                                  writes dL/dY, dL/dW, dL/dT of the bin and the
 //                                                  per-(bin, frame) terms kernel D needs
 //   D grad_vgather_kernel  (128 frames x 32 bins, source, mixture)  dL/dV += sum over those

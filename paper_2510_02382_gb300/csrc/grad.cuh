@@ -53,7 +53,7 @@ struct GradBufs {
 
 cudaError_t grad_configure(const Shape& s);
 size_t grad_act_partials(const Shape& s, int S);   // floats of GradBufs::actp
-// Enqueue the backward pass of one iteration (kernels A-D of grad.cu); gin selects the
+// Enqueue the backward pass of one iteration (kernels A-E of grad.cu); gin selects the
 // gV buffer that holds dL/dV'; the other receives dL/dV. first: the first iteration reversed,
 // whose normalisation sums kernel A forms (later ones get them from the per-bin adjoint of the
 // iteration reversed before, in g.e). Returns the kernels launched in *kernels.
